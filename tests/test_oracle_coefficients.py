@@ -1,0 +1,141 @@
+"""Pins of the oracle's coefficient tables (Remark anal_Fourier, eq. char_func_Four,
+eq. inclcomp_formula, Lemma integ_eval_VM).
+
+Each shape coefficient is checked against numerical quadrature of its defining
+integral f^(k) = int_Y f(x) exp(-2 pi i k.x) dx (Section 2.2), the shift sign
+against a direct 2-D quadrature of an off-centre disk, and the double-grid
+values against the bilinear form they must reproduce.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import j0
+
+from oracle import coefficients as C
+from oracle import fourier as F
+from oracle import galerkin as G
+
+
+@pytest.mark.parametrize("k", [(0, 0), (1, 0), (2, 3), (-5, 4)])
+def test_box_coefficient_quadrature(k):
+    h = (0.37, 0.81)
+    ref = 1.0
+    for a in range(2):
+        re = integrate.quad(lambda x: math.cos(2 * math.pi * k[a] * x), -h[a] / 2, h[a] / 2)[0]
+        ref *= re                       # the centred box is even: imaginary part 0
+    got = C.shape_coeff(C.BOX, np.array([k]), h)[0]
+    assert abs(got - ref) < 1e-12
+
+
+@pytest.mark.parametrize("k", [(0, 0), (1, 0), (3, 4), (-7, 2), (20, 13)])
+def test_disk_coefficient_hankel(k):
+    """Radial transform in 2-D: F(rho) = 2 pi int_0^r s J0(2 pi rho s) ds."""
+    r = 0.3090194
+    rho = math.hypot(*k)
+    ref = integrate.quad(lambda s: 2 * math.pi * s * j0(2 * math.pi * rho * s), 0, r, epsabs=1e-14, limit=200)[0]
+    got = C.shape_coeff(C.DISK, np.array([k]), (r,))[0]
+    assert abs(got - ref) < 1e-11
+
+
+@pytest.mark.parametrize("k", [(0, 0, 0), (0, 0, 1), (1, 2, 2), (5, -3, 7), (0.001, 0, 0)])
+def test_sphere_coefficient_radial(k):
+    """Radial transform in 3-D: F(rho) = 4 pi int_0^r s^2 sin(2 pi rho s)/(2 pi rho s) ds."""
+    r = 0.3627832
+    rho = math.sqrt(sum(v * v for v in k))
+
+    def f(s):
+        q = 2 * math.pi * rho * s
+        return 4 * math.pi * s * s * (math.sin(q) / q if q > 0 else 1.0)
+    ref = integrate.quad(f, 0, r, epsabs=1e-15, limit=200)[0]
+    got = C.shape_coeff(C.SPHERE, np.array([k], dtype=float), (r,))[0]
+    assert abs(got - ref) < 1e-12
+
+
+def test_sphere_fraction_radius():
+    r = (3 * 0.2 / (4 * math.pi)) ** (1 / 3)
+    assert abs(r - 0.3627832) < 1e-7
+    assert abs(C.shape_coeff(C.SPHERE, np.zeros((1, 3)), (r,))[0] - 0.2) < 1e-14
+
+
+@pytest.mark.parametrize("k", [(1, 0), (2, -3)])
+def test_shift_sign_offcentre_disk(k):
+    """f(x - x_i) has coefficient exp(-2 pi i k.x_i) f^(k): checked by a direct
+    2-D quadrature over the shifted disk (polar coordinates around x_i)."""
+    c = np.array([0.17, -0.23])
+    r = 0.2
+    mat = C.Material(2, 0.0, [C.Inclusion(C.DISK, tuple(c), (r,), 1.0)])
+
+    def integrand(t, s, part):
+        x = c + s * np.array([math.cos(t), math.sin(t)])
+        ph = -2 * math.pi * (k[0] * x[0] + k[1] * x[1])
+        return s * (math.cos(ph) if part == 0 else math.sin(ph))
+    re = integrate.dblquad(lambda t, s: integrand(t, s, 0), 0, r, 0, 2 * math.pi, epsabs=1e-13)[0]
+    im = integrate.dblquad(lambda t, s: integrand(t, s, 1), 0, r, 0, 2 * math.pi, epsabs=1e-13)[0]
+    got = C.coeff_at(mat, np.array([k]))[0]
+    assert abs(got - complex(re, im)) < 1e-10
+
+
+def test_table_hermitian_and_mean():
+    mat = C.Material(2, 2.0, [C.Inclusion(C.DISK, (0.1, 0.2), (0.2,), 7.0),
+                              C.Inclusion(C.BOX, (-0.3, -0.25), (0.2, 0.3), 0.5)])
+    t = C.coeff_table(mat, [9, 9])
+    assert np.allclose(t, np.conj(t[::-1, ::-1]), atol=1e-15)      # real coefficient
+    f1 = math.pi * 0.04
+    f2 = 0.06
+    assert abs(t[8, 8] - (2.0 + 5.0 * f1 - 1.5 * f2)) < 1e-14        # a^(0) = <a>
+    assert abs(mat.mean() - (2.0 + 5.0 * f1 - 1.5 * f2)) < 1e-14
+
+
+def _bilinear_dense(table, u, v):
+    """sum_{k,l} a^(l-k) u(k) conj(v(l)) -- the form of Lemma FD_matrix_full."""
+    A = G.dense_galerkin(table, u.shape)
+    return np.vdot(v.reshape(-1), A @ u.reshape(-1))
+
+
+@pytest.mark.parametrize("N,M", [((5, 5), (9, 9)), ((5, 7), (9, 14)), ((7, 7), (16, 15)),
+                                 ((3, 5, 3), (5, 9, 6))])
+def test_double_grid_quadrature_is_exact(N, M):
+    """Lemma integ_eval_VM: for M >= 2N-1, (1/|M|) sum_m A_M(x_m) u(x_m) v(x_m)
+    equals the exact integral sum_{k,l} a^(l-k) u^(k) conj(v^(l))."""
+    rng = np.random.default_rng(sum(N) + sum(M))
+    d = len(N)
+    incs = [C.Inclusion(C.BOX, tuple(rng.uniform(-0.5, 0.5, 3)), tuple(rng.uniform(0.1, 0.6, 3)), 4.0)]
+    if d == 2:
+        incs.append(C.Inclusion(C.DISK, (0.3, -0.2, 0), (0.15,), 9.0))
+    mat = C.Material(d, 1.5, incs)
+    table = C.coeff_table(mat, N)
+    aM = G.double_grid_values(table, M)
+    u = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    uM = F.idft_nd(F.pad_centred_to_wrapped(u, M), axes=range(d))
+    vM = F.idft_nd(F.pad_centred_to_wrapped(v, M), axes=range(d))
+    quad = np.sum(aM * uM * np.conj(vM)) / np.prod(M)
+    assert abs(quad - _bilinear_dense(table, u, v)) < 1e-12 * np.abs(table).sum() * np.abs(u).sum()
+    assert np.abs(np.imag(G.double_grid_values(table, M))).max() == 0
+
+
+def test_double_grid_too_coarse_aliases():
+    """A grid M = 2N-3 violates the lemma's hypothesis and the quadrature is no
+    longer exact (the bound on M is sharp), so a wrong M is caught."""
+    rng = np.random.default_rng(3)
+    N, M = (7, 7), (11, 11)
+    mat = C.Material(2, 1.0, [C.Inclusion(C.DISK, (0.1, 0.05), (0.3,), 10.0)])
+    table = C.coeff_table(mat, N)
+    padded = F.pad_centred_to_wrapped(table[1:-1, 1:-1], M)          # Z_{2N-3} part only
+    aM = F.idft_nd(padded, axes=range(2)).real
+    u = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    uM = F.idft_nd(F.pad_centred_to_wrapped(u, M), axes=range(2))
+    quad = np.sum(aM * uM * np.conj(uM)) / np.prod(M)
+    assert abs(quad - _bilinear_dense(table, u, u)) > 1e-6
+
+
+def test_validate_rejects_bad_inputs():
+    with pytest.raises(ValueError):
+        C.validate(C.Material(2, -1.0, []))
+    with pytest.raises(ValueError):
+        C.validate(C.Material(2, 1.0, [C.Inclusion(C.DISK, (0, 0), (0.6,), 2.0)]))
+    with pytest.raises(ValueError):   # overlapping through the periodic boundary
+        C.validate(C.Material(2, 1.0, [C.Inclusion(C.DISK, (0.45, 0), (0.1,), 2.0),
+                                       C.Inclusion(C.DISK, (-0.45, 0), (0.1,), 2.0)]))
