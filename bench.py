@@ -1,0 +1,416 @@
+"""Throughput of the Ga guaranteed-bounds hot path on GB300.
+
+One step = one bound pair of the measured workload: rebuild the coefficient
+tables a^, (1/a)^ on Z_{2N-1} and the double-grid values A_M, B_M from the
+inclusion list, then d primal and d dual CG solves with FP64 residual
+correction around FP32 inner iterations, the exact FP64 projection of every
+minimiser and the FP64 Gram energies -> upper and lower d x d bounds.
+
+Workload (default): d = 2, unit cell, one centred disk of volume fraction 0.3,
+contrast 100 (inclusion 100, matrix 1), N = 2187 (double grid 4374 x 4374),
+CG relative residual 1e-10; synthetic (seeded microstructure, nothing read).
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica on its own GPU (the solves shard by instance; no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "bound pairs/s & grid-pt·iter/s, mixed vs FP64 at 1e-8 rel err; p50/p99 latency"
+UNIT = "bound pairs/s"
+FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA peak: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (a plain FMA loop measured
+# 1.20 TFLOP/s on this part)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=2187)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the plain FP64 path (comparison)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(N):
+    import workloads as W
+    return W.centred_disk(N, fraction=0.3, value=100.0)
+
+
+def workload_name(N):
+    return f"d2 centred disk vf=0.3 contrast 100, N={N} (double grid {2 * N})"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import coefficients as C, galerkin as G
+m = W.centred_disk({N}, fraction=0.3, value=100.0)
+mat = C.material_from_dict(m)
+t0 = time.perf_counter()
+op = G.Operator(mat, m["N"], G.PRIMAL, M=[{M}, {M}])
+t_setup = time.perf_counter() - t0
+x = W.random_field(np.random.default_rng(1), 2, m["N"])
+ts = []
+for _ in range({reps}):
+    t0 = time.perf_counter()
+    op.apply(x)
+    ts.append(time.perf_counter() - t0)
+print(json.dumps(dict(setup_s=t_setup, matvec_s=ts)))
+"""
+
+
+def oracle_matvec_times(N, M, reps):
+    """Run the oracle (single-threaded numpy) in a child process: set-up time
+    and `reps` timed operator applications at the full workload size."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, N=N, M=M, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# operator applications of one FP64 bound pair at the default workload:
+# 2 primal + 2 dual CG solves (iterations measured on the FP64 GPU path, same
+# algorithm and tolerance) plus one application per admissible field for the
+# Gram energies.  Printed by the ours arm as "fp64.matvecs_per_pair".
+FP64_MATVECS_PER_PAIR = {2187: None}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    N = args.N
+    M = 2 * N
+    reps = max(1, args.steps)
+    mv_pair = FP64_MATVECS_PER_PAIR.get(N)
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; warm-up steps are not timed
+    res = oracle_matvec_times(N, M, reps)
+    t = sum(res["matvec_s"]) / len(res["matvec_s"])
+    mv = mv_pair if mv_pair else 4 * 100 + 4
+    value = 1.0 / (t * mv)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": reps, "warmup": args.warmup, "ms_per_step": 1e3 * t * mv, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(N), "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{reps} oracle operator applications at N={N}, M={M} "
+                                   f"(mean {t:.2f} s each), x {mv} applications per bound pair"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1412_2033_gb300 as g
+
+    torch.cuda.set_device(local)
+    g.load_library()
+    m = workload(args.N)
+    incs = m["inclusions"]
+
+    ctx = g.Context.from_microstructure(m, precision="mixed", tol=1e-10)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    for _ in range(args.warmup):
+        ctx.set_coeffs(m["a0"], incs)
+        ctx.bounds()
+
+    # ---- timed region: K steps on resident buffers, CUDA events on the context's stream
+    barrier(world)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    lat = []
+    U = L = infos = None
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.set_coeffs(m["a0"], incs)
+            U, L, infos, st = ctx.bounds()
+            e1.record(stream)
+            lat.append((e0, e1))
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    elapsed_max = allmax(world, elapsed)
+    pairs = args.steps * world
+    value = pairs / elapsed_max
+
+    iters32 = sum(i["matvecs_fp32"] for i in infos)
+    iters64 = sum(i["matvecs_fp64"] for i in infos)
+    grid_pts = float(np.prod(ctx.M))
+    gpi = (iters32 + iters64 + 2 * m["d"]) * grid_pts * args.steps * world / elapsed_max
+
+    # ---- roofline of the dominant kernel (from the live event timings above)
+    hbm, peak_src = peaks()
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    avg_s = dom["ms"] / dom["launches"] / 1e3
+    f32 = dom_name.endswith("_f32")
+    if f32 or dom["flops"] == 0:
+        achieved = dom["bytes"] / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": peak_src}
+    else:
+        achieved = dom["flops"] / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "derived FP64 FMA peak"}
+    roof["kernel"] = dom_name
+    roof["traffic"] = traffic_for(dom_name)
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "avg_us": round(1e3 * v["ms"] / v["launches"], 2),
+                   "GBps": round(v["bytes"] / (v["ms"] / v["launches"] / 1e3) / 1e9, 1) if v["bytes"] else None,
+                   "share": round(v["ms"] / sum(x["ms"] for x in prof.values()), 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    launches = sum(v["launches"] for v in prof.values())
+
+    # ---- plain FP64 path on the same workload (the comparison of the metric)
+    fp64 = None
+    if args.fp64_steps > 0:
+        c64 = g.Context.from_microstructure(m, precision="fp64", tol=1e-10)
+        c64.set_stream(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fp64_steps):
+            c64.set_coeffs(m["a0"], incs)
+            U64, L64, inf64, _ = c64.bounds()
+        torch.cuda.synchronize()
+        t64 = (time.perf_counter() - t0) / args.fp64_steps
+        mv64 = sum(i["matvecs_fp64"] for i in inf64) + 2 * m["d"]
+        err_u = float(np.abs(U - U64).max() / np.abs(U64).max())
+        err_l = float(np.abs(L - L64).max() / np.abs(L64).max())
+        fp64 = {"bound_pairs_per_s": 1.0 / t64, "s_per_pair": t64, "matvecs_per_pair": mv64,
+                "mixed_speedup": value / world / (1.0 / t64), "rel_err_upper": err_u, "rel_err_lower": err_l,
+                "upper": U64.tolist(), "lower": L64.tolist()}
+        c64.close()
+
+    # ---- end to end through the public API: host inclusion list in, host bounds out
+    e2e_ts = []
+    phase_bytes = 64 * max(1, len(incs))
+    out_bytes = 2 * m["d"] * m["d"] * 8
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = g.Context.from_microstructure(m, precision="mixed", tol=1e-10)
+        c.bounds()
+        c.close()
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_t = allmax(world, statistics.median(e2e_ts)) if e2e_ts else float("nan")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            res = oracle_matvec_times(args.N, ctx.M[0], 1)
+            t = res["matvec_s"][0]
+            mvp = fp64["matvecs_per_pair"] if fp64 else 4 * 100 + 4
+            cpu = {"value": 1.0 / (t * mvp), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"1 oracle operator application at N={args.N}, M={ctx.M[0]} ({t:.1f} s, "
+                             f"set-up {res['setup_s']:.1f} s) x {mvp} applications per FP64 bound pair"}
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded microstructure; nothing read from disk)",
+            "config": {"workload": workload_name(args.N), "N": [args.N, args.N], "M": ctx.M,
+                       "precision": "mixed: FP32 inner CG, FP64 residual correction, FP64 projection and Gram",
+                       "tol": 1e-10, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (per-step working set ~1.5 GB)"},
+            "grid_pt_iter_per_s": gpi,
+            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                            int(0.99 * len(lat_ms)))]},
+            "bounds": {"upper": U.tolist(), "lower": L.tolist()},
+            "solves": infos,
+            "fp64": fp64,
+            "roofline": roof,
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": {"value": pairs / e2e_t / args.steps * args.steps if e2e_ts else None, "unit": UNIT,
+                    "h2d_bytes_per_step": phase_bytes, "d2h_bytes_per_step": out_bytes,
+                    "what": "ghb_create (device set-up from the host inclusion list) + ghb_bounds "
+                            "(results to host) + ghb_destroy, host wall clock"},
+            "cpu_baseline": cpu,
+        }
+        if line["e2e"]["value"] is not None:
+            line["e2e"]["value"] = world / e2e_t
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def traffic_for(kernel_name):
+    """DRAM bytes per launch of `kernel_name` from the committed ncu summary,
+    or None when there is none or the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("sources_sha256") != sources_digest():
+            return None
+        return d.get("traffic_per_launch", {}).get(kernel_name)
+    except Exception:  # noqa: BLE001
+        return None
+
+
+def sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1412_2033_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

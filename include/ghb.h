@@ -1,0 +1,219 @@
+/*
+ * ghb.h -- guaranteed homogenization bounds, Ga scheme (Galerkin approximation
+ * with exact integration), GB300 (sm_103a) library.  C ABI.
+ *
+ * Method: J. Vondrejc, "Improved guaranteed computable bounds on homogenized
+ * properties of periodic media by Fourier-Galerkin method with exact
+ * integration", arXiv:1412.2033.
+ *
+ * Problem.  A scalar isotropic coefficient a(x) on the unit cell Y = (-1/2,1/2)^d,
+ * d in {2,3}, made of a matrix value a0 and disjoint inclusions (boxes, disks,
+ * spheres) -- the inclusion-matrix composite of eq. inclcomp.  For odd orders
+ * N = (N_1..N_d) the library computes the Ga bounds of Def. Ga:
+ *     upper U_ij = a(E_i + e_i, E_j + e_j),  e_i the minimiser over E_N (eq. GA_prim)
+ *     lower L = D^{-1},  D_ij = a^{-1}(J_i + j_i, J_j + j_j), j_i over J_N
+ * (Prop. struct_bounds, eq. spd_inverse_ineq), each minimiser found by conjugate
+ * gradients (Remark CG) on the projected system of Cor. Ga_linsys:
+ *     G A^full e = -G A^full E^,   G = G_E (primal) or G_J (dual, with 1/a).
+ * The operator is applied through a double grid M >= 2N-1 (Lemma
+ * integ_eval_VM, eq. MBA_GA, Algorithm 2): zero-pad Z_N -> Z_M, inverse FFT,
+ * multiply by A_M(x_m) = sum_{n in Z_{2N-1}} omega_M^{mn} a^(n), forward FFT,
+ * truncate to Z_N, project (Def. projection).
+ *
+ * Field layout (device memory, used by ghb_matvec and ghb_solve's output).
+ * A trial field is a real trigonometric polynomial of Def. trig_pol, stored by
+ * its Fourier coefficients as a half spectrum:
+ *     x[c][i_1]...[i_{d-1}][j]      c = 0..d-1 (vector component)
+ * i_a = 0..N_a-1 holds frequency k_a = i_a - (N_a-1)/2 (centred order);
+ * j = 0..(N_d-1)/2 holds k_d = j (the non-negative half of the last axis).
+ * Entries are complex: interleaved (re, im) pairs of double (FP64) or float
+ * (FP32).  The other half is implied by Hermitian symmetry x(-k) = conj x(k);
+ * on the plane k_d = 0 the caller must supply Hermitian-consistent entries.
+ * Number of complex entries: d * N_1 * ... * N_{d-1} * (N_d+1)/2
+ * (ghb_field_elems).
+ *
+ * Errors.  Every call returns a ghb_status; nothing aborts.  A failing call
+ * leaves a message for ghb_last_error() (per calling thread).
+ * Ownership.  Host arrays passed in are read during the call and copied;
+ * device pointers passed in stay owned by the caller.  A context owns all the
+ * device memory it allocates and frees it in ghb_destroy.
+ * Streams.  A context issues all of its work on one CUDA stream (its own, or
+ * the one given to ghb_set_stream).  ghb_solve_* and ghb_bounds return after
+ * the results are on the host.  ghb_matvec is asynchronous on its stream.
+ * Threads.  One context must not be used by two threads at the same time;
+ * distinct contexts are independent.
+ */
+#ifndef GHB_H
+#define GHB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ghb_ctx ghb_ctx;
+
+typedef enum {
+  GHB_OK = 0,
+  GHB_ERR_INVALID = 1,        /* bad argument: even N, d not 2/3, non-positive
+                                 coefficient, inclusion too large or overlapping,
+                                 unsupported M, null pointer */
+  GHB_ERR_OOM = 2,            /* device allocation failed */
+  GHB_ERR_NOT_CONVERGED = 3,  /* max_iter reached; outputs are still filled and
+                                 are still guaranteed bounds (any admissible
+                                 field gives one, Prop. struct_bounds) */
+  GHB_ERR_BREAKDOWN = 4,      /* CG curvature <p, Ap> not positive or not finite */
+  GHB_ERR_CUDA = 5            /* a CUDA runtime call failed */
+} ghb_status;
+
+typedef enum { GHB_BOX = 0, GHB_DISK = 1, GHB_SPHERE = 2 } ghb_shape;
+typedef enum { GHB_PRIMAL = 0, GHB_DUAL = 1 } ghb_kind;
+typedef enum {
+  GHB_FP64 = 0,   /* every operator application in FP64 */
+  GHB_MIXED = 1,  /* FP32 inner CG inside an FP64 residual-correction loop; the
+                     final projection and the bound energies in FP64 */
+  GHB_FP32 = 2    /* ghb_matvec only: the FP32 operator */
+} ghb_precision;
+
+/* One inclusion (eq. inclcomp): characteristic function of a centred shape
+ * moved to `center`, with coefficient `value` inside.
+ *   GHB_BOX:    size[0..d-1] = side lengths h_a, 0 < h_a <= 1 (rect_h)
+ *   GHB_DISK:   d = 2, size[0] = radius r, 0 < r <= 1/2     (circ_r)
+ *   GHB_SPHERE: d = 3, size[0] = radius r, 0 < r <= 1/2
+ * Fourier coefficients: Remark anal_Fourier, eq. char_func_Four; the sphere's
+ * is the three-dimensional radial transform (not printed in the paper). */
+typedef struct {
+  int32_t shape;
+  int32_t pad_;
+  double center[3];
+  double size[3];
+  double value;
+} ghb_phase;
+
+typedef struct {
+  double tol;          /* CG stop: ||r||_2 / ||b||_2 <= tol (default 1e-10) */
+  int32_t max_iter;    /* per solve, counted in operator applications (default 20000) */
+  int32_t precision;   /* GHB_FP64 (default) or GHB_MIXED */
+  double inner_tol;    /* GHB_MIXED: relative reduction asked of each FP32 inner
+                          solve (default 1e-5) */
+  int32_t max_outer;   /* GHB_MIXED: cap on FP64 residual corrections (default 20) */
+  int32_t M[3];        /* double grid per axis; 0 = automatic: the smallest
+                          M_a >= 2 N_a - 1 whose prime factors are 2, 3, 5.
+                          Any M_a >= 2 N_a - 1 whose prime factors are <= 31
+                          is accepted (Lemma integ_eval_VM: the bilinear form
+                          does not depend on M). */
+} ghb_options;
+
+typedef struct {
+  int32_t status;        /* ghb_status of this solve */
+  int32_t iters;         /* CG iterations (all inner iterations for GHB_MIXED) */
+  int32_t outer_iters;   /* FP64 residual corrections (GHB_MIXED), else 0 */
+  int32_t matvecs_fp64;  /* FP64 operator applications */
+  int32_t matvecs_fp32;  /* FP32 operator applications */
+  int32_t pad_;
+  double relres;         /* final ||r||/||b|| of the FP64 system */
+  double energy;         /* a(E+e, E+e) (primal) or a^{-1}(J+j, J+j) (dual), FP64 */
+} ghb_solve_info;
+
+/* Default options (tol 1e-10, FP64, automatic M). */
+void ghb_default_options(ghb_options* opt);
+
+/* Create a context for dimension d, odd orders N[0..d-1], matrix value a0 and
+ * n_phases inclusions.  Builds, on the device, the coefficient tables a^ and
+ * (1/a)^ on Z_{2N-1} (eq. inclcomp_formula) and their double-grid values A_M,
+ * B_M (eq. MBA_GA).  `opt` may be NULL for defaults.  On success *out owns the
+ * context; on failure *out is NULL. */
+ghb_status ghb_create(ghb_ctx** out, int d, const int* N, double a0,
+                      const ghb_phase* phases, int n_phases, const ghb_options* opt);
+
+/* Replace the microstructure (same d, N, M): rebuild a^, (1/a)^, A_M, B_M. */
+ghb_status ghb_set_coeffs(ghb_ctx* ctx, double a0, const ghb_phase* phases, int n_phases);
+
+/* Replace the options of an existing context (M is fixed at creation and ignored). */
+ghb_status ghb_set_options(ghb_ctx* ctx, const ghb_options* opt);
+
+/* Use `stream` (a cudaStream_t, or NULL for the context's own) for all work. */
+ghb_status ghb_set_stream(ghb_ctx* ctx, void* stream);
+
+/* Grid sizes: N_out[0..d-1], M_out[0..d-1] (may be NULL) and the number of
+ * complex entries of one field in the half-spectrum layout above. */
+ghb_status ghb_get_grid(const ghb_ctx* ctx, int* d_out, int* N_out, int* M_out,
+                        int64_t* field_elems);
+int64_t ghb_field_elems(const ghb_ctx* ctx);
+
+/* y = G A^full x (kind = GHB_PRIMAL: G_E and a; GHB_DUAL: G_J and 1/a) for one
+ * field in the half-spectrum layout; precision GHB_FP64 (double pairs) or
+ * GHB_FP32 (float pairs).  x_dev, y_dev: device pointers, caller-owned, not
+ * overlapping.  project = 0 skips G (returns A^full x, used for energies).
+ * Asynchronous on `stream` (NULL = the context's stream). */
+ghb_status ghb_matvec(ghb_ctx* ctx, int kind, int precision, int project,
+                      const void* x_dev, void* y_dev, void* stream);
+
+/* Minimise a(E + e, E + e) over e in E_N (primal) or a^{-1}(J + j, J + j)
+ * over j in J_N (dual) for the load E[0..d-1].  If field_out_dev is not NULL
+ * the admissible field E + e (FP64 half spectrum) is written there.  `info`
+ * (may be NULL) receives iterations, residual and the FP64 energy. */
+ghb_status ghb_solve_primal(ghb_ctx* ctx, const double* E, void* field_out_dev,
+                            ghb_solve_info* info);
+ghb_status ghb_solve_dual(ghb_ctx* ctx, const double* J, void* field_out_dev,
+                          ghb_solve_info* info);
+
+/* The Gram matrix out[i*m + j] = a(v_i, v_j) (kind primal) or a^{-1}(v_i, v_j)
+ * (dual) of m <= 3 FP64 fields v_i given as device pointers, evaluated exactly
+ * on the double grid in FP64 (Lemma integ_eval_VM): (1/|M|) sum_m A_M(x_m)
+ * v_i(x_m).v_j(x_m).  Synchronous. */
+ghb_status ghb_gram(ghb_ctx* ctx, int kind, int m, const void* const* fields_dev,
+                    double* out);
+
+/* Both bounds: d primal and d dual solves with unit loads, then the Gram
+ * matrices; upper[d*d] = U, lower[d*d] = D^{-1} (row-major, symmetrised).
+ * infos (may be NULL) receives 2d entries: primal e_1..e_d, dual e_1..e_d. */
+ghb_status ghb_bounds(ghb_ctx* ctx, double* upper, double* lower, ghb_solve_info* infos);
+
+/* Device data for checks: the coefficient table a^ (kind primal) or (1/a)^
+ * (dual) on Z_{2N-1} as a half spectrum (centred leading axes of length
+ * 2N_a-1, last axis n_d = 0..N_d-1; complex FP64), or the double-grid values
+ * A_M / B_M (real FP64, C-order over m_a = 0..M_a-1, grid point x = m/M).
+ * `out_dev` must hold the stated number of entries (ghb_table_elems /
+ * ghb_grid_elems).  Synchronous. */
+int64_t ghb_table_elems(const ghb_ctx* ctx);
+int64_t ghb_grid_elems(const ghb_ctx* ctx);
+ghb_status ghb_copy_table(ghb_ctx* ctx, int kind, void* out_dev);
+ghb_status ghb_copy_grid_values(ghb_ctx* ctx, int kind, void* out_dev);
+
+/* Timing of the context's own launches.  ghb_profile(ctx, 1) starts recording a
+ * pair of CUDA events around every kernel launch on the context's stream
+ * (launches queued after a CG solve ended are dropped), ghb_profile(ctx, 0)
+ * stops; both clear earlier records.  ghb_profile_read sums the records of one
+ * kernel class: cls = 2 * k + f, f = 1 for the FP32 variant, k one of
+ *   0 coefficient set-up, 1 axis-1 inverse pass fused with the CG direction
+ *   update, 2 axis-1 inverse pass, 3 axis-2 inverse pass, 4 last-axis pass
+ *   (inverse, multiply by A_M, forward), 5 axis-2 forward pass, 6 axis-1
+ *   forward pass with truncation, 7 projection + <p, Ap>, 8 CG vector update
+ *   + <r, r>, 9 projection, 10 FP64 residual, 11 Gram pass, 12 other.
+ * It returns the number of launches, their summed duration in ms, and the
+ * algorithmic bytes and FFT flops (5 L log2 L per length-L complex transform)
+ * of one launch of that class for this context's sizes. */
+ghb_status ghb_profile(ghb_ctx* ctx, int enable);
+ghb_status ghb_profile_read(ghb_ctx* ctx, int cls, int64_t* launches, double* total_ms,
+                            double* bytes_per_launch, double* flops_per_launch);
+
+/* Device bytes held by the context. */
+int64_t ghb_device_bytes(const ghb_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ghb_last_error(void);
+
+/* Release the context and all device memory it owns.  NULL is a no-op. */
+void ghb_destroy(ghb_ctx* ctx);
+
+/* Library version string. */
+const char* ghb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GHB_H */

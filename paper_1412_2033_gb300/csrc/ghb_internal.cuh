@@ -1,0 +1,177 @@
+// Internal declarations of the ghb library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+#include "../../include/ghb.h"
+
+namespace ghb {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+#define GHB_CUDA_TRY(expr)                                                     \
+  do {                                                                         \
+    cudaError_t err__ = (expr);                                                \
+    if (err__ != cudaSuccess) {                                                \
+      ::ghb::set_error(std::string(#expr) + ": " + cudaGetErrorString(err__)); \
+      return err__ == cudaErrorMemoryAllocation ? GHB_ERR_OOM : GHB_ERR_CUDA;  \
+    }                                                                          \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device-side CG scalars (one per running solve)
+// ---------------------------------------------------------------------------
+enum DoneCode { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, MAXITER = 3 };
+
+struct CgState {
+  double rr;       // <r, r> (full-spectrum inner product)
+  double pq;       // <p, A p>
+  double alpha;
+  double beta;
+  double bb;       // <b, b>
+  double tol2;     // stop when rr <= tol2 (= tol^2 bb)
+  int iter;
+  int maxiter;
+  int done;        // DoneCode
+  int pad;
+  unsigned int ticket;  // last-block counter of the running reduction
+  unsigned int pad2;
+};
+
+constexpr int kMaxPartials = 4096;
+
+// ---------------------------------------------------------------------------
+// inclusions on the device
+// ---------------------------------------------------------------------------
+struct Incl {
+  int shape;
+  int pad;
+  double c[3];
+  double s[3];
+  double dv;       // (inside value - matrix value) of the coefficient tabulated
+};
+
+// ---------------------------------------------------------------------------
+// geometry of one context
+// ---------------------------------------------------------------------------
+struct Geometry {
+  int d;
+  int N[3];
+  int M[3];
+  int h;                  // (N_d + 1)/2: stored half of the last axis
+  int64_t P;              // complex entries per component of a field
+  int64_t field;          // d * P
+  int64_t T1;             // entries of the axis-1 intermediate (all components)
+  int64_t T2;             // entries of the axis-2 intermediate (d = 3)
+  int64_t rows;           // rows of the last-axis pass: M_1 (d=2), M_1 M_2 (d=3)
+  int64_t grid;           // |M|
+  int64_t table;          // entries of the half table on Z_{2N-1}
+};
+
+// Host-owned plan with its device tables.
+struct PlanHolder {
+  FftPlan plan{};
+  int* d_perm = nullptr;
+  double2* d_tw64 = nullptr;
+  float2* d_tw32 = nullptr;
+};
+
+ghb_status make_plan(int M, PlanHolder& out);
+void free_plan(PlanHolder& p);
+bool factorizable(int M);
+int auto_M(int N);
+
+// ---------------------------------------------------------------------------
+// launchers (kernels.cu)
+// ---------------------------------------------------------------------------
+enum ColMode { COL_PLAIN = 0, COL_PUPDATE = 1 };
+
+// Column pass: transforms along a non-contiguous axis.  Arrays are viewed as
+// [outer][L][inner]; `in` has L = Lin, `out` has L = Lout.
+//  sign = +1: zero-pad (input index i is frequency i - (Lin-1)/2), inverse DFT
+//             of length M, output rows m = 0..M-1 (Lout = M).
+//  sign = -1: forward DFT of the M input rows, keep frequencies of Z_Lout
+//             (centred), scale by 1/M.
+struct ColArgs {
+  const void* in;
+  void* out;
+  const void* pold;   // COL_PUPDATE: p_old (read), written back as p = in + beta p_old
+  void* pnew;
+  const CgState* st;  // COL_PUPDATE: beta; early exit when done
+  int64_t outer, inner;
+  int Lin, Lout;
+};
+
+template <typename T>
+ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
+
+enum RowMode { ROW_MATVEC = 0, ROW_TOREAL = 1, ROW_ENERGY = 2 };
+
+// Row pass along the contiguous half-spectrum axis.
+struct RowArgs {
+  void* t[3];          // per field: [c][row][H] complex half spectra (MATVEC: in place)
+  int nfields;
+  int ncomp;           // components per field
+  int64_t rows;
+  int H;               // stored half length (h for fields, N_d for the table)
+  int64_t comp_stride; // entries between components (= rows * H)
+  const void* a;       // [row][M] real multiplier (MATVEC, ENERGY)
+  void* out_real;      // [row][M] real output (TOREAL)
+  double* partials;    // ENERGY: per-block partial Gram
+  double* gram;        // ENERGY: final Gram (nfields^2), scaled by 1/|M|
+  unsigned int* ticket;
+  double scale;        // ENERGY: 1/|M|
+  const CgState* st;   // MATVEC: early exit when done (may be null)
+};
+
+template <typename T>
+ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_t s);
+
+// Field-level kernels (half-spectrum fields of one context).
+struct FieldGeom {
+  int d;
+  int N[3];
+  int h;
+  int64_t P;
+};
+
+ghb_status launch_coeff_table(double2* tab, const Geometry& g, const Incl* incs, int n, double a0v,
+                              cudaStream_t s);
+template <typename T>
+ghb_status launch_rhs(void* b, const double2* tab, const Geometry& g, const double* E, int kind,
+                      cudaStream_t s);
+template <typename T>
+ghb_status launch_project(void* y, const void* w, const FieldGeom& fg, int kind, cudaStream_t s);
+template <typename T>
+ghb_status launch_cg_init(void* x, void* r, void* p, const void* b, const FieldGeom& fg, CgState* st,
+                          double* partials, double tol, int maxiter, cudaStream_t s);
+template <typename T>
+ghb_status launch_project_dot(void* q, const void* w, const void* p, const FieldGeom& fg, int kind,
+                              CgState* st, double* partials, cudaStream_t s);
+template <typename T>
+ghb_status launch_update(void* x, void* r, const void* p, const void* q, const FieldGeom& fg,
+                         CgState* st, double* partials, cudaStream_t s);
+// r64 = b64 - y64, rr into st (FP64 outer residual); also st->done reset
+ghb_status launch_residual(double2* r, const double2* b, const double2* y, const FieldGeom& fg,
+                           CgState* st, double* partials, cudaStream_t s);
+ghb_status launch_to_f32(float2* dst, const double2* src, int64_t n, cudaStream_t s);
+ghb_status launch_accum_f32(double2* x, const float2* dx, int64_t n, cudaStream_t s);
+ghb_status launch_to_f32_real(float* dst, const double* src, int64_t n, cudaStream_t s);
+ghb_status launch_add_constant(double2* v, const double2* e, const FieldGeom& fg, const double* E,
+                               cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// shared-memory sizing
+// ---------------------------------------------------------------------------
+int col_tile_width(int M, int elem_bytes);
+size_t col_smem_bytes(int M, int TW, int elem_bytes);
+
+}  // namespace ghb

@@ -1,0 +1,328 @@
+"""Python binding of the ghb C ABI (include/ghb.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library ``lib/libghb.so``; this module
+loads it with ctypes, converts arguments, and uses PyTorch only for device
+memory and streams.  There is no CPU fallback: if the library is missing or
+cannot be loaded, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB
+
+GHB_OK, GHB_ERR_INVALID, GHB_ERR_OOM, GHB_ERR_NOT_CONVERGED, GHB_ERR_BREAKDOWN, GHB_ERR_CUDA = range(6)
+GHB_BOX, GHB_DISK, GHB_SPHERE = 0, 1, 2
+GHB_PRIMAL, GHB_DUAL = 0, 1
+GHB_FP64, GHB_MIXED, GHB_FP32 = 0, 1, 2
+
+STATUS_NAMES = {0: "GHB_OK", 1: "GHB_ERR_INVALID", 2: "GHB_ERR_OOM", 3: "GHB_ERR_NOT_CONVERGED",
+                4: "GHB_ERR_BREAKDOWN", 5: "GHB_ERR_CUDA"}
+
+# every symbol include/ghb.h declares
+EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_options", "ghb_set_stream",
+           "ghb_get_grid", "ghb_field_elems", "ghb_matvec", "ghb_solve_primal", "ghb_solve_dual",
+           "ghb_gram", "ghb_bounds", "ghb_table_elems", "ghb_grid_elems", "ghb_copy_table",
+           "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
+           "ghb_profile", "ghb_profile_read"]
+
+PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
+                   "project_dot", "update", "project", "residual", "gram_row", "misc"]
+
+
+class GhbPhase(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("pad_", ctypes.c_int32), ("center", ctypes.c_double * 3),
+                ("size", ctypes.c_double * 3), ("value", ctypes.c_double)]
+
+
+class GhbOptions(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("M", ctypes.c_int32 * 3)]
+
+
+class GhbSolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+                ("matvecs_fp64", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("relres", ctypes.c_double), ("energy", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class GhbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB) -> ctypes.CDLL:
+    """Load lib/libghb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"ghb CUDA library not built: {path} is missing "
+                          "(run paper_1412_2033_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "ghb_default_options": (None, [ctypes.POINTER(GhbOptions)]),
+        "ghb_create": (i32, [ctypes.POINTER(P), i32, ip, dbl, ctypes.POINTER(GhbPhase), i32,
+                             ctypes.POINTER(GhbOptions)]),
+        "ghb_set_coeffs": (i32, [P, dbl, ctypes.POINTER(GhbPhase), i32]),
+        "ghb_set_options": (i32, [P, ctypes.POINTER(GhbOptions)]),
+        "ghb_set_stream": (i32, [P, P]),
+        "ghb_get_grid": (i32, [P, ip, ip, ip, ctypes.POINTER(i64)]),
+        "ghb_field_elems": (i64, [P]),
+        "ghb_matvec": (i32, [P, i32, i32, i32, P, P, P]),
+        "ghb_solve_primal": (i32, [P, dp, P, ctypes.POINTER(GhbSolveInfo)]),
+        "ghb_solve_dual": (i32, [P, dp, P, ctypes.POINTER(GhbSolveInfo)]),
+        "ghb_gram": (i32, [P, i32, i32, ctypes.POINTER(P), dp]),
+        "ghb_bounds": (i32, [P, dp, dp, ctypes.POINTER(GhbSolveInfo)]),
+        "ghb_table_elems": (i64, [P]),
+        "ghb_grid_elems": (i64, [P]),
+        "ghb_copy_table": (i32, [P, i32, P]),
+        "ghb_copy_grid_values": (i32, [P, i32, P]),
+        "ghb_device_bytes": (i64, [P]),
+        "ghb_last_error": (ctypes.c_char_p, []),
+        "ghb_destroy": (None, [P]),
+        "ghb_version": (ctypes.c_char_p, []),
+        "ghb_profile": (i32, [P, i32]),
+        "ghb_profile_read": (i32, [P, i32, ctypes.POINTER(i64), dp, dp, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != GHB_OK:
+        raise GhbError(status, _lib.ghb_last_error().decode())
+    return status
+
+
+def make_phases(inclusions):
+    """ctypes array of GhbPhase from (shape, center, size, value) tuples."""
+    n = len(inclusions)
+    arr = (GhbPhase * max(n, 1))()
+    for i, (shape, center, size, value) in enumerate(inclusions):
+        arr[i].shape = int(shape)
+        for a in range(3):
+            arr[i].center[a] = float(center[a]) if a < len(center) else 0.0
+            arr[i].size[a] = float(size[a]) if a < len(size) else 0.0
+        arr[i].value = float(value)
+    return arr, n
+
+
+@dataclass
+class Options:
+    tol: float = 1e-10
+    max_iter: int = 20000
+    precision: str = "fp64"          # "fp64" or "mixed"
+    inner_tol: float = 1e-5
+    max_outer: int = 20
+    M: tuple = (0, 0, 0)
+
+    def to_c(self):
+        o = GhbOptions()
+        load_library().ghb_default_options(ctypes.byref(o))
+        o.tol = self.tol
+        o.max_iter = self.max_iter
+        o.precision = {"fp64": GHB_FP64, "mixed": GHB_MIXED}[self.precision]
+        o.inner_tol = self.inner_tol
+        o.max_outer = self.max_outer
+        for a in range(3):
+            o.M[a] = int(self.M[a]) if a < len(self.M) else 0
+        return o
+
+
+class Context:
+    """One microstructure at one order N on the current CUDA device (C ABI ghb_ctx)."""
+
+    def __init__(self, d, N, a0, inclusions, **options):
+        lib = load_library()
+        self.d = int(d)
+        self.opts = Options(**options)
+        Nc = (ctypes.c_int * 3)(*([int(n) for n in N] + [1] * (3 - len(N))))
+        ph, n = make_phases(inclusions)
+        self._h = ctypes.c_void_p()
+        opt = self.opts.to_c()
+        _check(lib.ghb_create(ctypes.byref(self._h), self.d, Nc, float(a0), ph, n, ctypes.byref(opt)))
+        dd = ctypes.c_int()
+        Nn = (ctypes.c_int * 3)()
+        Mm = (ctypes.c_int * 3)()
+        fe = ctypes.c_int64()
+        _check(lib.ghb_get_grid(self._h, ctypes.byref(dd), Nn, Mm, ctypes.byref(fe)))
+        self.N = [Nn[a] for a in range(self.d)]
+        self.M = [Mm[a] for a in range(self.d)]
+        self.field_elems = fe.value
+        self.h = (self.N[-1] + 1) // 2
+
+    @classmethod
+    def from_microstructure(cls, m: dict, **options):
+        return cls(m["d"], m["N"], m["a0"], m["inclusions"], **options)
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ghb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration --------------------------------------------------------
+    @property
+    def field_shape(self):
+        """Shape of one half-spectrum field: (d, N_1, .., N_{d-1}, (N_d+1)/2)."""
+        return (self.d, *self.N[:-1], self.h)
+
+    def set_coeffs(self, a0, inclusions):
+        ph, n = make_phases(inclusions)
+        _check(_lib.ghb_set_coeffs(self._h, float(a0), ph, n))
+
+    def set_options(self, **options):
+        for k, v in options.items():
+            setattr(self.opts, k, v)
+        o = self.opts.to_c()
+        _check(_lib.ghb_set_options(self._h, ctypes.byref(o)))
+
+    def set_stream(self, stream):
+        """Use a torch.cuda.Stream (or None for the context's own stream)."""
+        ptr = None if stream is None else stream.cuda_stream
+        _check(_lib.ghb_set_stream(self._h, ptr))
+
+    def device_bytes(self):
+        return int(_lib.ghb_device_bytes(self._h))
+
+    def profile(self, enable=True):
+        _check(_lib.ghb_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{class name + ('_f32'|'_f64'): dict(launches, ms, bytes, flops)} of the recorded launches."""
+        out = {}
+        for k, name in enumerate(PROFILE_CLASSES):
+            for f in (0, 1):
+                n = ctypes.c_int64()
+                ms, b, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+                _check(_lib.ghb_profile_read(self._h, 2 * k + f, ctypes.byref(n), ctypes.byref(ms),
+                                             ctypes.byref(b), ctypes.byref(fl)))
+                if n.value:
+                    out[name + ("_f32" if f else "_f64")] = dict(launches=n.value, ms=ms.value, bytes=b.value,
+                                                                  flops=fl.value)
+        return out
+
+    # -- operator -------------------------------------------------------------
+    def matvec(self, x, kind=GHB_PRIMAL, project=True, out=None, stream=None):
+        """y = G A^full x on the device for a half-spectrum field x (torch
+        complex128 -> FP64 operator, complex64 -> FP32 operator)."""
+        import torch
+        if x.dtype == torch.complex128:
+            prec = GHB_FP64
+        elif x.dtype == torch.complex64:
+            prec = GHB_FP32
+        else:
+            raise TypeError("x must be complex128 or complex64")
+        if tuple(x.shape) != self.field_shape or not x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous CUDA tensor of shape {self.field_shape}")
+        y = torch.empty_like(x) if out is None else out
+        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        if s is None:
+            s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        _check(_lib.ghb_matvec(self._h, int(kind), prec, int(bool(project)), ctypes.c_void_p(x.data_ptr()),
+                               ctypes.c_void_p(y.data_ptr()), s))
+        return y
+
+    # -- solves ---------------------------------------------------------------
+    def solve(self, kind, E, want_field=False):
+        """Minimiser for load E; returns (info dict, field or None).  A status of
+        GHB_ERR_NOT_CONVERGED is reported in info, not raised."""
+        import torch
+        Ec = (ctypes.c_double * 3)(*([float(e) for e in E] + [0.0] * (3 - len(E))))
+        field = torch.empty(self.field_shape, dtype=torch.complex128, device="cuda") if want_field else None
+        inf = GhbSolveInfo()
+        fn = _lib.ghb_solve_primal if kind == GHB_PRIMAL else _lib.ghb_solve_dual
+        st = fn(self._h, Ec, ctypes.c_void_p(field.data_ptr()) if want_field else None, ctypes.byref(inf))
+        if st not in (GHB_OK, GHB_ERR_NOT_CONVERGED):
+            _check(st)
+        return inf.as_dict(), field
+
+    def gram(self, kind, fields):
+        ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in fields])
+        out = (ctypes.c_double * 9)()
+        _check(_lib.ghb_gram(self._h, int(kind), len(fields), ptrs, out))
+        m = len(fields)
+        return np.array(out[: m * m]).reshape(m, m)
+
+    def bounds(self):
+        """(upper, lower, infos): the d x d Ga bounds and 2d solve records."""
+        d = self.d
+        up = (ctypes.c_double * 9)()
+        lo = (ctypes.c_double * 9)()
+        infos = (GhbSolveInfo * 6)()
+        st = _lib.ghb_bounds(self._h, up, lo, infos)
+        if st not in (GHB_OK, GHB_ERR_NOT_CONVERGED):
+            _check(st)
+        U = np.array(up[: d * d]).reshape(d, d)
+        L = np.array(lo[: d * d]).reshape(d, d)
+        return U, L, [infos[i].as_dict() for i in range(2 * d)], st
+
+    # -- data for checks --------------------------------------------------------
+    def table(self, kind=GHB_PRIMAL):
+        """a^ (or (1/a)^) on Z_{2N-1}, half spectrum, as a complex128 CUDA tensor."""
+        import torch
+        shape = tuple(2 * n - 1 for n in self.N[:-1]) + (self.N[-1],)
+        t = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        _check(_lib.ghb_copy_table(self._h, int(kind), ctypes.c_void_p(t.data_ptr())))
+        return t
+
+    def grid_values(self, kind=GHB_PRIMAL):
+        """A_M (or B_M) on the double grid, float64 CUDA tensor of shape M."""
+        import torch
+        t = torch.empty(tuple(self.M), dtype=torch.float64, device="cuda")
+        _check(_lib.ghb_copy_grid_values(self._h, int(kind), ctypes.c_void_p(t.data_ptr())))
+        return t
+
+
+# ---------------------------------------------------------------------------
+# layout helpers (index permutations and conjugation only)
+# ---------------------------------------------------------------------------
+def half_from_full(x):
+    """(d, N_1..N_d) centred full spectrum -> (d, N_1..N_{d-1}, (N_d+1)/2) half spectrum."""
+    Nd = x.shape[-1]
+    return x[..., (Nd - 1) // 2:]
+
+
+def full_from_half(xh, Nd):
+    """Inverse of half_from_full using x(-k) = conj x(k) (numpy arrays)."""
+    xh = np.asarray(xh)
+    d = xh.ndim - 1
+    c = (Nd - 1) // 2
+    out = np.zeros(xh.shape[:-1] + (Nd,), dtype=xh.dtype)
+    out[..., c:] = xh
+    # k_d < 0: x(k', -j) = conj x(-k', j) with k' mirrored on the leading axes
+    mirrored = np.conj(xh[(slice(None),) + (slice(None, None, -1),) * (d - 1) + (slice(1, None),)])
+    out[..., :c] = mirrored[..., ::-1]
+    return out
