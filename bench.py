@@ -48,6 +48,14 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the plain FP64 path (comparison)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="instances of the batched workload (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window of the served workload (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--matvec-only", choices=["f32", "f64"], default=None,
+                    help="only apply the operator (warmup + steps times) at the workload size; "
+                         "prints the mean time per application (used for ncu captures)")
     return ap.parse_args()
 
 
@@ -330,6 +338,9 @@ def run_ours(args, world, rank, local):
         e2e_ts.append(time.perf_counter() - t0)
     e2e_t = allmax(world, statistics.median(e2e_ts)) if e2e_ts else float("nan")
 
+    batched = run_batched(args, g) if args.batch_count > 0 else None
+    served = run_served(args, g) if args.serve_seconds > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -358,6 +369,8 @@ def run_ours(args, world, rank, local):
             "bounds": {"upper": U.tolist(), "lower": L.tolist()},
             "solves": infos,
             "fp64": fp64,
+            "batched": batched,
+            "served": served,
             "roofline": roof,
             "kernels": kernels,
             "gpu_launches": launches,
@@ -372,6 +385,94 @@ def run_ours(args, world, rank, local):
             line["e2e"]["value"] = world / e2e_t
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def run_batched(args, g):
+    """The 512-instance workload: K ~ U{1..20} disks of radius U(0.03, 0.12),
+    contrast log-uniform in [2, 1e4], N odd uniform in 31..255; all instances
+    solved together by the batch engine (one launch per kernel and CG
+    iteration over every active solve).  Compared with the plain FP64
+    single-solve path on a sample of the same instances."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    inst = W.disk_batch(args.batch_count)
+    b = g.Batch()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in inst:
+        b.submit(m)
+    b.run(iterations=8)
+    t = time.perf_counter() - t0
+    res = {r["id"]: r for r in b.results()}
+    st = b.stats()
+    b.close()
+    ok = sum(1 for r in res.values() if r["status"] == 0)
+    iters = [sum(i["iters"] for i in r["infos"]) for r in res.values()]
+    # plain FP64 single-solve GPU path on a sample
+    sample = inst[: min(8, len(inst))]
+    errs = []
+    t64 = 0.0
+    ids = sorted(res)
+    for k, m in enumerate(sample):
+        c = g.Context.from_microstructure(m, precision="fp64", tol=1e-10)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        U, L, _, _ = c.bounds()
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t1
+        c.close()
+        r = res[ids[k]]
+        errs.append(max(float(np.abs(r["upper"] - U).max() / np.abs(U).max()),
+                        float(np.abs(r["lower"] - L).max() / np.abs(L).max())))
+    fp64_rate = len(sample) / t64
+    return {"workload": f"{len(inst)} seeded d2 disk instances, N odd 31..255, contrast 2..1e4",
+            "bound_pairs_per_s": len(inst) / t, "seconds": t, "ok": ok,
+            "cg_iterations_per_pair_mean": float(np.mean(iters)), "launches": st["launches"],
+            "fp64_single_solve_pairs_per_s": fp64_rate, "fp64_sample": len(sample),
+            "speedup_vs_fp64_single": (len(inst) / t) / fp64_rate,
+            "max_rel_err_vs_fp64_sample": max(errs) if errs else None}
+
+
+def run_served(args, g):
+    """Poisson arrivals (rate per second) of bound requests mixing d = 2 disk
+    instances (N odd 63..1023) and d = 3 sphere instances (N odd 15..129),
+    submitted as they arrive into one batch (continuous batching).  Latency =
+    arrival -> result on the host clock."""
+    import numpy as np
+
+    import workloads as W
+    stream = W.request_stream(rate=args.serve_rate, duration=args.serve_seconds)
+    b = g.Batch()
+    t0 = time.perf_counter()
+    arrivals = {}
+    done = {}
+    i = 0
+    deadline = args.serve_seconds + 120.0
+    while (i < len(stream) or len(done) < i) and time.perf_counter() - t0 < deadline:
+        now = time.perf_counter() - t0
+        while i < len(stream) and stream[i][0] <= now:
+            rid = b.submit(stream[i][1])
+            arrivals[rid] = stream[i][0]
+            i += 1
+        if len(done) < i:
+            b.step(iterations=4)
+            tnow = time.perf_counter() - t0
+            for r in b.results():
+                done[r["id"]] = (tnow, r["status"])
+        else:
+            time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    b.close()
+    lat = sorted(done[k][0] - arrivals[k] for k in done)
+    n2 = sum(1 for _, m in stream[:i] if m["d"] == 2)
+    return {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, "
+                        f"d2 disks N 63..1023 / d3 spheres N 15..129",
+            "submitted": i, "completed": len(done), "d2": n2, "d3": i - n2,
+            "bound_pairs_per_s": len(done) / wall, "wall_s": wall,
+            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2] if lat else None,
+                           "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None}}
 
 
 def traffic_for(kernel_name):
@@ -400,9 +501,39 @@ def sources_digest():
     return h.hexdigest()
 
 
+def run_matvec_only(args, local):
+    import numpy as np
+    import torch
+
+    import paper_1412_2033_gb300 as g
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    m = workload(args.N)
+    ctx = g.Context.from_microstructure(m)
+    dt = torch.complex64 if args.matvec_only == "f32" else torch.complex128
+    x = torch.from_numpy(np.ascontiguousarray(g.half_from_full(
+        W.random_field(np.random.default_rng(0), m["d"], m["N"])))).to(dt).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        ctx.matvec(x, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.matvec(x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"matvec": args.matvec_only, "N": args.N, "M": ctx.M,
+                      "ms_per_matvec": e0.elapsed_time(e1) / max(1, args.steps)}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
+    if args.matvec_only:
+        run_matvec_only(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -200,6 +200,58 @@ ghb_status ghb_profile(ghb_ctx* ctx, int enable);
 ghb_status ghb_profile_read(ghb_ctx* ctx, int cls, int64_t* launches, double* total_ms,
                             double* bytes_per_launch, double* flops_per_launch);
 
+/* ------------------------------------------------------------------------
+ * Batched and served solving.  A batch holds many bound-pair requests (each
+ * one microstructure at its own d and N) and solves them together in the
+ * mixed scheme: every CG iteration is one launch per kernel over all active
+ * solves, whatever their sizes.  Requests are admitted while their device
+ * memory (coefficient grids, CG vectors, intermediates of their 2d solves)
+ * fits the batch's budget, so requests submitted while others run join the
+ * running work at the next step (continuous batching); finished requests leave
+ * and free their memory.  A batch owns its CUDA stream and device memory.
+ * ------------------------------------------------------------------------ */
+typedef struct ghb_batch ghb_batch;
+
+typedef struct {
+  int64_t id;              /* as returned by ghb_batch_submit */
+  int32_t d;
+  int32_t status;          /* ghb_status of the request */
+  double upper[9];         /* d x d row-major */
+  double lower[9];
+  ghb_solve_info info[6];  /* primal e_1..e_d, then dual e_1..e_d */
+  double seconds_queued;   /* submission -> admission (host clock) */
+  double seconds_total;    /* submission -> result */
+} ghb_result;
+
+/* Create a batch.  opt: NULL for defaults (precision must be GHB_MIXED);
+ * budget_bytes: device-memory budget for admitted requests (0 = 60% of the
+ * free memory now); max_active: cap on requests solved at once (0 = 4096). */
+ghb_status ghb_batch_create(ghb_batch** out, const ghb_options* opt, int64_t budget_bytes, int max_active);
+
+/* Queue one bound-pair request (same microstructure description and checks as
+ * ghb_create).  Host arrays are copied.  *id_out receives its id. */
+ghb_status ghb_batch_submit(ghb_batch* b, int d, const int* N, double a0, const ghb_phase* phases,
+                            int n_phases, int64_t* id_out);
+
+/* One engine cycle: admit pending requests that fit, run `iterations` batched
+ * FP32 CG iterations (0 = 8) over all active solves, apply the FP64
+ * corrections of solves whose inner CG ended, and finish the requests whose
+ * solves all ended.  Synchronises with the device.  *active_out, *pending_out
+ * (may be NULL) receive the counts after the cycle. */
+ghb_status ghb_batch_step(ghb_batch* b, int iterations, int* active_out, int* pending_out);
+
+/* Step until every submitted request has finished. */
+ghb_status ghb_batch_run(ghb_batch* b, int iterations);
+
+/* Move up to max_results finished results into out[]; returns how many. */
+int ghb_batch_results(ghb_batch* b, ghb_result* out, int max_results);
+
+ghb_status ghb_batch_stats(const ghb_batch* b, int64_t* bytes_in_use, int* active, int* pending,
+                           int64_t* finished, int64_t* launches);
+
+/* Release the batch (pending and running requests are dropped).  NULL is a no-op. */
+void ghb_batch_destroy(ghb_batch* b);
+
 /* Device bytes held by the context. */
 int64_t ghb_device_bytes(const ghb_ctx* ctx);
 

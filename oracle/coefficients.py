@@ -78,7 +78,16 @@ class Material:
 
 
 def _sinc(x):
-    return np.sinc(x)  # sin(pi x)/(pi x), 1 at 0 -- the paper's sinc
+    """sin(pi x)/(pi x), 1 at 0 (the paper's sinc, Remark anal_Fourier).
+
+    sin(pi x) is evaluated after reducing x modulo 2 (exact in binary floating
+    point), so large arguments keep full relative accuracy."""
+    x = np.asarray(x, dtype=np.float64)
+    red = x - 2.0 * np.round(0.5 * x)
+    out = np.ones_like(x)
+    nz = x != 0
+    out[nz] = np.sin(np.pi * red[nz]) / (np.pi * x[nz])
+    return out
 
 
 def shape_coeff(shape: int, k: np.ndarray, size) -> np.ndarray:
@@ -127,7 +136,9 @@ def coeff_at(mat: Material, n: np.ndarray) -> np.ndarray:
     out[np.all(n == 0, axis=-1)] += mat.a0
     for inc in mat.inclusions:
         xi = np.asarray(inc.center, dtype=np.float64)[: mat.d]
-        phase = np.exp(-2j * np.pi * (n.astype(np.float64) @ xi))
+        t = n.astype(np.float64) @ xi
+        t = t - np.round(t)          # exp(-2 pi i t) is 1-periodic in t: reduce first
+        phase = np.exp(-2j * np.pi * t)
         out += (inc.value - mat.a0) * phase * shape_coeff(inc.shape, n, inc.size)
     return out
 

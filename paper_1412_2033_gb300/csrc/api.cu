@@ -530,7 +530,7 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
         done = MAXITER;
         break;
       }
-      PROF(c, PK_MISC, true, launch_to_f32(c->w32.w, r64, g.field, c->stream));
+      PROF(c, PK_MISC, true, launch_to_f32(c->w32.w, r64, fg, c->stream));
       // q32 holds the FP32 right-hand side for the inner solve
       GHB_CUDA_TRY(cudaMemcpyAsync(c->w32.q, c->w32.w, sizeof(float2) * g.field,
                                    cudaMemcpyDeviceToDevice, c->stream));
@@ -544,7 +544,7 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
         done = BREAKDOWN;
         break;
       }
-      PROF(c, PK_MISC, false, launch_accum_f32(c->w64.x, c->w32.x, g.field, c->stream));
+      PROF(c, PK_MISC, false, launch_accum_f32(c->w64.x, c->w64.x, c->w32.x, fg, c->stream));
       // exact FP64 projection onto the admissible (real, curl- or divergence-free) fields
       PROF(c, PK_PROJECT, false, launch_project<double>(x64, c->w64.x, fg, kind, c->stream));
       GHB_CUDA_TRY(cudaMemcpyAsync(c->w64.x, x64, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice,

@@ -1,0 +1,14 @@
+// Instantiations of the transform-pass kernels (see passes_impl.cuh).
+#include "passes_impl.cuh"
+
+namespace ghb {
+
+template ghb_status launch_col_tw<double, 1>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
+template ghb_status launch_col_tw<double, 2>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
+template ghb_status launch_col_tw<double, 4>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
+
+template ghb_status launch_col_batch_tw<double, 1>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_col_batch_tw<double, 2>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_col_batch_tw<double, 4>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+
+}  // namespace ghb

@@ -10,20 +10,28 @@
 // factor is applied by the caller when it truncates to Z_N).
 //
 // Data layout in shared memory: NL independent lines interleaved,
-// buf[m * NL + line], so that consecutive threads touch consecutive words.
+// element (m, line) at padded index pad(m * NL + line), so that consecutive
+// threads touch consecutive words and strided butterflies spread over banks.
 //
-// Algorithms (in place, one shared buffer, one barrier per stage):
-//  * fft_dit: decimation in time.  Input in mixed-radix digit-reversed order
-//    (the caller scatters x[n] to position perm[n]), output in natural order.
-//    Stage t (radix R_t, L_{t-1} = R_1...R_{t-1}, L_t = L_{t-1} R_t) combines
-//    R_t transforms of length L_{t-1}: for block b and position p < L_{t-1} the
-//    butterfly reads the R_t entries b L_t + p + q L_{t-1}, multiplies entry q by
-//    w_{L_t}^{pq}, applies DFT_{R_t} and writes back in place.
-//  * fft_dif: decimation in frequency, the same stages in reverse order with
-//    the twiddle applied after the small DFT.  Input natural, output
-//    digit-reversed (X[k] ends at position perm[k]).
-// The pair lets a line go inverse (DIT) -> pointwise multiply in natural order
-// -> forward (DIF) without any permutation pass.
+// Algorithm (in place, one shared buffer).  M = R_1 ... R_s (radices 2,3,4,5 or
+// a prime <= 31).  Decimation in time (DIT) takes digit-reversed input (the
+// caller scatters x[n] to position perm[n]) and returns natural order; stage t
+// combines R_t transforms of length L_{t-1} = R_1...R_{t-1}: for block b and
+// position p < L_{t-1} the butterfly reads the R_t entries b L_t + p + q L_{t-1},
+// multiplies entry q by w_{L_t}^{pq}, applies DFT_{R_t} and writes back.
+// Decimation in frequency (DIF) runs the same stages in reverse order with the
+// twiddle after the small DFT: natural input, digit-reversed output (X[k] at
+// perm[k]).  A line therefore goes inverse (DIT) -> pointwise multiply ->
+// forward (DIF) without any permutation pass.
+//
+// Register blocking: consecutive stages are grouped into passes of at most
+// three stages (radix product <= 32).  The stages of a group act inside the
+// sets {b L_g + p + j L_{t-1} : j < R_g}, so one thread loads such a set into
+// registers, runs the group's stages there and writes it back: one shared-memory
+// round trip and one barrier per pass instead of per stage.  Twiddles: the
+// stage-s factor w_{L_s}^{(p + j' L_{t-1}) q} = (w_{L_s}^p w_{sigma rho}^{j'})^q is a
+// table load per pass and sub-stage (w_{L_s}^p) times a root of unity of small
+// order held in constant memory, raised to the power q by multiplication.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,7 +40,49 @@
 namespace ghb {
 
 constexpr int kMaxStages = 24;
+constexpr int kMaxPasses = 24;
 constexpr int kMaxGenericRadix = 31;
+constexpr int kMaxRootOrder = 32;     // roots w_n^k tabulated for n <= 32
+
+// Division by an invariant 32-bit integer with a multiply-high (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// round-up variant): q = (t + ((n - t) >> 1)) >> (l - 1), t = umulhi(n, m),
+// m = floor(2^32 (2^l - d) / d) + 1, l = ceil(log2 d).  Exact for every 32-bit n.
+struct FastDiv {
+  unsigned d;
+  unsigned m;
+  int l;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  f.l = l;
+  if (d == 1) {
+    f.m = 0;
+  } else {
+    const unsigned long long num = (1ull << 32) * ((1ull << l) - d);
+    f.m = static_cast<unsigned>(num / d + 1);
+  }
+  return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+  if (f.d == 1) return n;
+  const unsigned t = __umulhi(n, f.m);
+  return (t + ((n - t) >> 1)) >> (f.l - 1);
+}
+
+// Shapes of one pass: the radices of its stages in DIT order.
+enum PassShape {
+  SH_2 = 0, SH_3, SH_4, SH_5,
+  SH_2_3, SH_3_3, SH_2_5, SH_4_3, SH_3_5, SH_4_4, SH_4_5, SH_5_5, SH_4_2,
+  SH_2_3_3, SH_3_3_3, SH_4_2_3, SH_2_3_5, SH_4_4_2,
+  SH_GENERIC,   // one stage of a prime radix 7..31 (O(R^2) definition)
+  SH_COUNT
+};
 
 // Plan of one length-M transform.  Tables live in device memory.
 struct FftPlan {
@@ -40,9 +90,18 @@ struct FftPlan {
   int nst;                   // number of stages
   int R[kMaxStages];         // radix of DIT stage t
   int Lp[kMaxStages];        // L_{t-1}: product of the radices before stage t
+  // passes per precision ([0] FP64: at most 18 entries per thread so the
+  // registers hold them; [1] FP32: at most 32)
+  int npass[2];
+  int pshape[2][kMaxPasses];    // PassShape of each pass (DIT order)
+  int pR[2][kMaxPasses];        // radix product of the pass (or the prime)
+  int pLp[2][kMaxPasses];       // L_{t-1} of its first stage
+  FastDiv pdiv[2][kMaxPasses];  // division by pLp
   const int* perm;           // perm[n]: digit-reversed position of index n
   const double2* tw64;       // tw64[j] = exp(-2 pi i j / M)
   const float2* tw32;        // the same rounded to float
+  const double2* roots64;    // roots of unity of order <= 32 (see croot)
+  const float2* roots32;
 };
 
 template <typename T> struct CT;
@@ -58,7 +117,12 @@ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return mk(a.x 
 __device__ __forceinline__ double2 operator*(double s, double2 a) { return mk(s * a.x, s * a.y); }
 __device__ __forceinline__ float2 operator*(float s, float2 a) { return mk(s * a.x, s * a.y); }
 
-// a * w (SIGN = -1) or a * conj(w) (SIGN = +1); w from the forward table.
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// a * w (SIGN = -1) or a * conj(w) (SIGN = +1); w in the forward convention.
 template <int SIGN, typename C>
 __device__ __forceinline__ C twmul(C a, C w) {
   if (SIGN < 0) return mk(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
@@ -74,8 +138,35 @@ __device__ __forceinline__ C rot(C a) {
 template <typename C> __device__ __forceinline__ const C* twtab(const FftPlan& p);
 template <> __device__ __forceinline__ const double2* twtab<double2>(const FftPlan& p) { return p.tw64; }
 template <> __device__ __forceinline__ const float2* twtab<float2>(const FftPlan& p) { return p.tw32; }
+template <typename C> __device__ __forceinline__ const C* roottab(const FftPlan& p);
+template <> __device__ __forceinline__ const double2* roottab<double2>(const FftPlan& p) { return p.roots64; }
+template <> __device__ __forceinline__ const float2* roottab<float2>(const FftPlan& p) { return p.roots32; }
 
-// Small DFTs X_k = sum_n x_n exp(SIGN 2 pi i n k / R), in registers.
+// Padded shared-memory index: one spare slot every 128 bytes of data.
+template <typename C>
+__device__ __forceinline__ int pidx(int i) {
+  return sizeof(C) == 8 ? i + (i >> 4) : i + (i >> 3);
+}
+template <typename C>
+__host__ __device__ inline size_t padded_elems(size_t n) {
+  return sizeof(C) == 8 ? n + (n >> 4) + 1 : n + (n >> 3) + 1;
+}
+
+// ---------------------------------------------------------------------------
+// roots of unity of small order (a per-plan device table, read with uniform
+// addresses so a warp's load is one broadcast transaction):
+//   roots[n (n - 1) / 2 + k] = exp(-2 pi i k / n),  1 <= n <= 32, k < n
+// ---------------------------------------------------------------------------
+constexpr int kRootTable = kMaxRootOrder * (kMaxRootOrder + 1) / 2;
+
+template <typename C>
+__device__ __forceinline__ C croot(const C* __restrict__ roots, int n, int k) {
+  return __ldg(&roots[n * (n - 1) / 2 + k]);
+}
+
+// ---------------------------------------------------------------------------
+// small DFTs X_k = sum_n x_n exp(SIGN 2 pi i n k / R), in registers
+// ---------------------------------------------------------------------------
 template <int SIGN, typename C>
 __device__ __forceinline__ void dft2(C* v) {
   C a = v[0], b = v[1];
@@ -128,116 +219,197 @@ __device__ __forceinline__ void dft5(C* v) {
 
 template <int SIGN, int R, typename C>
 __device__ __forceinline__ void dft_small(C* v) {
-  if (R == 2) dft2<SIGN>(v);
-  else if (R == 3) dft3<SIGN>(v);
-  else if (R == 4) dft4<SIGN>(v);
-  else if (R == 5) dft5<SIGN>(v);
+  if constexpr (R == 2) dft2<SIGN>(v);
+  else if constexpr (R == 3) dft3<SIGN>(v);
+  else if constexpr (R == 4) dft4<SIGN>(v);
+  else if constexpr (R == 5) dft5<SIGN>(v);
 }
 
-// Butterfly of a specialised radix.  DIT: twiddle, then DFT; DIF: DFT, then twiddle.
-template <int SIGN, int R, bool DIT, typename C>
-__device__ __forceinline__ void bfly(C* buf, int base, int step, int twj, const C* tw) {
-  C v[R];
+// ---------------------------------------------------------------------------
+// one sub-stage of a register-blocked pass
+//   RHO: radix of the stage, SIG: product of the radices before it inside the
+//   pass, RG: radix product of the whole pass; v holds the pass's RG entries
+//   (entry j at position b L_g + p + j Lp).  ts = M / (Lp SIG RHO).
+// ---------------------------------------------------------------------------
+template <int SIGN, bool DIT, int RHO, int SIG, int RG, typename C>
+__device__ __forceinline__ void substage(C* v, int p, int ts, const C* __restrict__ tw,
+                                         const C* __restrict__ roots) {
+  const C wb = __ldg(&tw[p * ts]);   // w_{L_s}^p, L_s = Lp SIG RHO
 #pragma unroll
-  for (int q = 0; q < R; ++q) v[q] = buf[base + q * step];
-  if (DIT) {
+  for (int jp = 0; jp < SIG; ++jp) {
+    C t1 = (jp == 0) ? wb : cmul(wb, croot<C>(roots, SIG * RHO, jp));
+    C tq[RHO];
+    tq[0] = mk(decltype(wb.x)(1), decltype(wb.x)(0));
+    if constexpr (RHO > 1) tq[1] = t1;
 #pragma unroll
-    for (int q = 1; q < R; ++q) v[q] = twmul<SIGN>(v[q], __ldg(&tw[q * twj]));
-  }
-  dft_small<SIGN, R>(v);
-  if (!DIT) {
+    for (int q = 2; q < RHO; ++q) tq[q] = cmul(tq[q - 1], t1);
 #pragma unroll
-    for (int q = 1; q < R; ++q) v[q] = twmul<SIGN>(v[q], __ldg(&tw[q * twj]));
-  }
+    for (int jb = 0; jb < RG / (SIG * RHO); ++jb) {
+      C e[RHO];
 #pragma unroll
-  for (int q = 0; q < R; ++q) buf[base + q * step] = v[q];
-}
-
-// Butterfly of any radix R <= kMaxGenericRadix by the O(R^2) definition, with
-// the R-th roots of unity taken from the length-M table (R divides M).
-template <int SIGN, bool DIT, typename C>
-__device__ void bfly_generic(C* buf, int base, int step, int twj, int R, int M, const C* tw) {
-  C v[kMaxGenericRadix];
-  C o[kMaxGenericRadix];
-  const int MR = M / R;
-  for (int q = 0; q < R; ++q) {
-    v[q] = buf[base + q * step];
-    if (DIT && q > 0) v[q] = twmul<SIGN>(v[q], __ldg(&tw[q * twj]));
-  }
-  for (int k = 0; k < R; ++k) {
-    C acc = v[0];
-    int e = 0;
-    for (int n = 1; n < R; ++n) {
-      e += k;
-      if (e >= R) e -= R;
-      acc = acc + twmul<SIGN>(v[n], __ldg(&tw[e * MR]));
-    }
-    o[k] = acc;
-  }
-  for (int q = 0; q < R; ++q) {
-    C r = o[q];
-    if (!DIT && q > 0) r = twmul<SIGN>(r, __ldg(&tw[q * twj]));
-    buf[base + q * step] = r;
-  }
-}
-
-// Stage metadata copied to shared memory once per kernel (avoids dynamic
-// indexing of kernel-parameter arrays).
-struct StageSmem {
-  int R[kMaxStages];
-  int Lp[kMaxStages];
-};
-
-__device__ __forceinline__ void load_stages(StageSmem& s, const FftPlan& p) {
+      for (int q = 0; q < RHO; ++q) e[q] = v[jb * SIG * RHO + jp + q * SIG];
+      if (DIT) {
 #pragma unroll
-  for (int i = 0; i < kMaxStages; ++i) {
-    if (threadIdx.x == 0) {
-      s.R[i] = p.R[i];
-      s.Lp[i] = p.Lp[i];
+        for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
+      }
+      dft_small<SIGN, RHO>(e);
+      if (!DIT) {
+#pragma unroll
+        for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RHO; ++q) v[jb * SIG * RHO + jp + q * SIG] = e[q];
     }
   }
 }
 
-// One stage over NL interleaved lines.
+// A pass of up to three stages (radices RA, RB, RC in DIT order; 1 = absent).
+template <int SIGN, bool DIT, int NL, int RA, int RB, int RC, typename C>
+__device__ __forceinline__ void run_pass(C* buf, int M, int Lp, const FastDiv& dv,
+                                         const C* __restrict__ tw, const C* __restrict__ roots) {
+  constexpr int RG = RA * RB * RC;
+  const int units = M / RG;
+  const int tsA = M / (Lp * RA);
+  const int tsB = tsA / RB;
+  const int tsC = tsB / RC;
+  for (int u = threadIdx.x; u < units * NL; u += blockDim.x) {
+    const int line = (NL == 1) ? 0 : u % NL;
+    const int unit = (NL == 1) ? u : u / NL;
+    const int b = static_cast<int>(fdiv(static_cast<unsigned>(unit), dv));
+    const int p = unit - b * Lp;
+    const int base = (b * Lp * RG + p) * NL + line;
+    const int step = Lp * NL;
+    C v[RG];
+#pragma unroll
+    for (int j = 0; j < RG; ++j) v[j] = buf[pidx<C>(base + j * step)];
+    if (DIT) {
+      substage<SIGN, DIT, RA, 1, RG>(v, p, tsA, tw, roots);
+      if constexpr (RB > 1) substage<SIGN, DIT, RB, RA, RG>(v, p, tsB, tw, roots);
+      if constexpr (RC > 1) substage<SIGN, DIT, RC, RA * RB, RG>(v, p, tsC, tw, roots);
+    } else {
+      if constexpr (RC > 1) substage<SIGN, DIT, RC, RA * RB, RG>(v, p, tsC, tw, roots);
+      if constexpr (RB > 1) substage<SIGN, DIT, RB, RA, RG>(v, p, tsB, tw, roots);
+      substage<SIGN, DIT, RA, 1, RG>(v, p, tsA, tw, roots);
+    }
+#pragma unroll
+    for (int j = 0; j < RG; ++j) buf[pidx<C>(base + j * step)] = v[j];
+  }
+}
+
+// One stage of a prime radix R <= kMaxGenericRadix by the O(R^2) definition,
+// with the R-th roots of unity taken from the length-M table (R divides M).
 template <int SIGN, bool DIT, int NL, typename C>
-__device__ __forceinline__ void fft_stage(C* buf, int M, int R, int Lp, const C* tw) {
+__device__ void run_generic(C* buf, int M, int R, int Lp, const FastDiv& dv, const C* __restrict__ tw) {
+  const int units = M / R;
   const int Lt = Lp * R;
-  const int nb = M / R;
-  const int tws = M / Lt;
-  const int total = nb * NL;
-  for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int line = (NL == 1) ? 0 : (u % NL);
-    const int beta = (NL == 1) ? u : (u / NL);
-    const int b = beta / Lp;
-    const int p = beta - b * Lp;
+  const int ts = M / Lt;
+  const int MR = M / R;
+  for (int u = threadIdx.x; u < units * NL; u += blockDim.x) {
+    const int line = (NL == 1) ? 0 : u % NL;
+    const int unit = (NL == 1) ? u : u / NL;
+    const int b = static_cast<int>(fdiv(static_cast<unsigned>(unit), dv));
+    const int p = unit - b * Lp;
     const int base = (b * Lt + p) * NL + line;
     const int step = Lp * NL;
-    const int twj = p * tws;
-    switch (R) {
-      case 2: bfly<SIGN, 2, DIT>(buf, base, step, twj, tw); break;
-      case 3: bfly<SIGN, 3, DIT>(buf, base, step, twj, tw); break;
-      case 4: bfly<SIGN, 4, DIT>(buf, base, step, twj, tw); break;
-      case 5: bfly<SIGN, 5, DIT>(buf, base, step, twj, tw); break;
-      default: bfly_generic<SIGN, DIT>(buf, base, step, twj, R, M, tw); break;
+    C v[kMaxGenericRadix];
+    C o[kMaxGenericRadix];
+    for (int q = 0; q < R; ++q) {
+      v[q] = buf[pidx<C>(base + q * step)];
+      if (DIT && q > 0) v[q] = twmul<SIGN>(v[q], __ldg(&tw[q * p * ts]));
     }
+    for (int k = 0; k < R; ++k) {
+      C acc = v[0];
+      int e = 0;
+      for (int n = 1; n < R; ++n) {
+        e += k;
+        if (e >= R) e -= R;
+        acc = acc + twmul<SIGN>(v[n], __ldg(&tw[e * MR]));
+      }
+      o[k] = acc;
+    }
+    for (int q = 0; q < R; ++q) {
+      C r = o[q];
+      if (!DIT && q > 0) r = twmul<SIGN>(r, __ldg(&tw[q * p * ts]));
+      buf[pidx<C>(base + q * step)] = r;
+    }
+  }
+}
+
+// Pass metadata copied to shared memory once per kernel (avoids dynamic
+// indexing of kernel-parameter arrays).
+struct PassSmem {
+  int shape[kMaxPasses];
+  int R[kMaxPasses];
+  int Lp[kMaxPasses];
+  FastDiv dv[kMaxPasses];
+};
+
+template <typename C>
+__device__ __forceinline__ int load_passes(PassSmem& s, const FftPlan& p) {
+  constexpr int k = sizeof(C) == 8 ? 1 : 0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < kMaxPasses; ++i) {
+      s.shape[i] = p.pshape[k][i];
+      s.R[i] = p.pR[k][i];
+      s.Lp[i] = p.pLp[k][i];
+      s.dv[i] = p.pdiv[k][i];
+    }
+  }
+  return p.npass[k];
+}
+
+// Passes wider than 18 entries run only in FP32 (the FP64 plans never use them,
+// and leaving them out keeps the FP64 kernels' register allocation small).
+template <int SIGN, bool DIT, int NL, int RA, int RB, int RC, typename C>
+__device__ __forceinline__ void run_pass_p(C* buf, int M, int Lp, const FastDiv& dv,
+                                           const C* __restrict__ tw, const C* __restrict__ roots) {
+  if constexpr (sizeof(C) == 8 || RA * RB * RC <= 18) run_pass<SIGN, DIT, NL, RA, RB, RC>(buf, M, Lp, dv, tw, roots);
+}
+
+template <int SIGN, bool DIT, int NL, typename C>
+__device__ __forceinline__ void dispatch_pass(C* buf, int M, const PassSmem& ps, int i,
+                                              const C* __restrict__ tw, const C* __restrict__ roots) {
+  const int Lp = ps.Lp[i];
+  const FastDiv dv = ps.dv[i];
+  switch (ps.shape[i]) {
+    case SH_2: run_pass_p<SIGN, DIT, NL, 2, 1, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_3: run_pass_p<SIGN, DIT, NL, 3, 1, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4: run_pass_p<SIGN, DIT, NL, 4, 1, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_5: run_pass_p<SIGN, DIT, NL, 5, 1, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_2_3: run_pass_p<SIGN, DIT, NL, 2, 3, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_3_3: run_pass_p<SIGN, DIT, NL, 3, 3, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_2_5: run_pass_p<SIGN, DIT, NL, 2, 5, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4_3: run_pass_p<SIGN, DIT, NL, 4, 3, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_3_5: run_pass_p<SIGN, DIT, NL, 3, 5, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4_4: run_pass_p<SIGN, DIT, NL, 4, 4, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4_5: run_pass_p<SIGN, DIT, NL, 4, 5, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_5_5: run_pass_p<SIGN, DIT, NL, 5, 5, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4_2: run_pass_p<SIGN, DIT, NL, 4, 2, 1>(buf, M, Lp, dv, tw, roots); break;
+    case SH_2_3_3: run_pass_p<SIGN, DIT, NL, 2, 3, 3>(buf, M, Lp, dv, tw, roots); break;
+    case SH_3_3_3: run_pass_p<SIGN, DIT, NL, 3, 3, 3>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4_2_3: run_pass_p<SIGN, DIT, NL, 4, 2, 3>(buf, M, Lp, dv, tw, roots); break;
+    case SH_2_3_5: run_pass_p<SIGN, DIT, NL, 2, 3, 5>(buf, M, Lp, dv, tw, roots); break;
+    case SH_4_4_2: run_pass_p<SIGN, DIT, NL, 4, 4, 2>(buf, M, Lp, dv, tw, roots); break;
+    default: run_generic<SIGN, DIT, NL>(buf, M, ps.R[i], Lp, dv, tw); break;
   }
 }
 
 // Decimation in time: digit-reversed input -> natural output.  The caller
 // must __syncthreads() after filling buf; returns after a final barrier.
 template <int SIGN, int NL, typename C>
-__device__ void fft_dit(C* buf, const StageSmem& st, int nst, int M, const C* tw) {
-  for (int s = 0; s < nst; ++s) {
-    fft_stage<SIGN, true, NL>(buf, M, st.R[s], st.Lp[s], tw);
+__device__ void fft_dit(C* buf, const PassSmem& ps, int npass, int M, const C* tw, const C* roots) {
+  for (int i = 0; i < npass; ++i) {
+    dispatch_pass<SIGN, true, NL>(buf, M, ps, i, tw, roots);
     __syncthreads();
   }
 }
 
 // Decimation in frequency: natural input -> digit-reversed output.
 template <int SIGN, int NL, typename C>
-__device__ void fft_dif(C* buf, const StageSmem& st, int nst, int M, const C* tw) {
-  for (int s = nst - 1; s >= 0; --s) {
-    fft_stage<SIGN, false, NL>(buf, M, st.R[s], st.Lp[s], tw);
+__device__ void fft_dif(C* buf, const PassSmem& ps, int npass, int M, const C* tw, const C* roots) {
+  for (int i = npass - 1; i >= 0; --i) {
+    dispatch_pass<SIGN, false, NL>(buf, M, ps, i, tw, roots);
     __syncthreads();
   }
 }

@@ -25,19 +25,20 @@ int field_grid(int64_t n) {
   return static_cast<int>(b);
 }
 
-__device__ __forceinline__ void kvec(const FieldGeom& g, int64_t e, int k[3], int& j) {
+__device__ __forceinline__ void kvec(const FieldGeom& g, int64_t e64, int k[3], int& j) {
+  // 32-bit index arithmetic: a field has fewer than 2^31 entries per component
+  const unsigned e = static_cast<unsigned>(e64);
+  const unsigned h = static_cast<unsigned>(g.h);
+  const unsigned i12 = e / h;
+  j = static_cast<int>(e - i12 * h);
   if (g.d == 2) {
-    const int64_t i1 = e / g.h;
-    j = static_cast<int>(e - i1 * g.h);
-    k[0] = static_cast<int>(i1) - (g.N[0] - 1) / 2;
+    k[0] = static_cast<int>(i12) - (g.N[0] - 1) / 2;
     k[1] = j;
     k[2] = 0;
   } else {
-    const int64_t plane = static_cast<int64_t>(g.N[1]) * g.h;
-    const int64_t i1 = e / plane;
-    const int64_t rem = e - i1 * plane;
-    const int64_t i2 = rem / g.h;
-    j = static_cast<int>(rem - i2 * g.h);
+    const unsigned n1 = static_cast<unsigned>(g.N[1]);
+    const unsigned i1 = i12 / n1;
+    const unsigned i2 = i12 - i1 * n1;
     k[0] = static_cast<int>(i1) - (g.N[0] - 1) / 2;
     k[1] = static_cast<int>(i2) - (g.N[1] - 1) / 2;
     k[2] = j;
@@ -46,16 +47,12 @@ __device__ __forceinline__ void kvec(const FieldGeom& g, int64_t e, int k[3], in
 
 // Index of the entry holding -k for an entry on the plane k_d = 0 (where both
 // k and -k are stored); -1 elsewhere.
-__device__ __forceinline__ int64_t mirror_index(const FieldGeom& g, int64_t e, int j) {
+__device__ __forceinline__ int64_t mirror_index(const FieldGeom& g, const int k[3], int j) {
   if (j != 0) return -1;
-  if (g.d == 2) {
-    const int64_t i1 = e / g.h;
-    return (g.N[0] - 1 - i1) * g.h;
-  }
-  const int64_t i12 = e / g.h;
-  const int64_t i1 = i12 / g.N[1];
-  const int64_t i2 = i12 - i1 * g.N[1];
-  return ((g.N[0] - 1 - i1) * g.N[1] + (g.N[1] - 1 - i2)) * g.h;
+  const int i1 = (g.N[0] - 1) / 2 - k[0];
+  if (g.d == 2) return static_cast<int64_t>(i1) * g.h;
+  const int i2 = (g.N[1] - 1) / 2 - k[1];
+  return (static_cast<int64_t>(i1) * g.N[1] + i2) * g.h;
 }
 
 // Real part of a field on Z_N (Def. trig_pol: admissible fields are real
@@ -96,21 +93,23 @@ __device__ __forceinline__ void project_vec(int d, const int k[3], int kind, con
 
 // Grid-wide sum: partial per block, the last block to finish adds the
 // partials in block order.  Returns true in thread 0 of that block with *total.
-__device__ bool grid_sum_last(double v, double* partials, unsigned int* ticket, double* total) {
+// `bid`, `nb`: this block and the number of blocks working on the same operand.
+__device__ bool grid_sum_last(double v, double* partials, unsigned int* ticket, double* total,
+                              int64_t bid, int64_t nb) {
   __shared__ double red[32];
   __shared__ bool last;
   const double bs = block_sum(v, red);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bs;
+    partials[bid] = bs;
     __threadfence();
     const unsigned int t = atomicAdd(ticket, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == nb - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
   double s = 0.0;
-  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(&partials[b]);
+  for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(&partials[b]);
   s = block_sum(s, red);
   if (threadIdx.x == 0) {
     *ticket = 0u;
@@ -128,6 +127,63 @@ __device__ double sinc_pi(double x) {   // sin(pi x)/(pi x)
   return x == 0.0 ? 1.0 : sinpi(x) / (kPi * x);
 }
 
+// Bessel function of the first kind of order one.
+//  |x| <= 8: CUDA's j1 (accurate to a few ulp there).
+//  8 < |x| < 20: Miller's backward recurrence J_{n-1} = (2n/x) J_n - J_{n+1},
+//     started at n0 ~ |x| + 40 with J_{n0+1} = 0, normalised by the identity
+//     J_0 + 2 sum_{k>=1} J_{2k} = 1.
+//  |x| >= 20: Hankel's asymptotic expansion (Abramowitz and Stegun 9.2.5,
+//     9.2.9-9.2.10): J_1(x) = sqrt(2/(pi x)) (P cos chi - Q sin chi),
+//     chi = x - 3 pi/4, P = sum_k (-1)^k a_{2k} x^{-2k},
+//     Q = sum_k (-1)^k a_{2k+1} x^{-2k-1},
+//     a_m = prod_{j=1..m} (4 - (2j-1)^2) / (m! 8^m); summed until the terms
+//     fall below 1e-18 (the smallest term is about e^{-2x}).
+// CUDA's j1 loses about 1e-12 relative to the envelope sqrt(2/(pi x)) beyond
+// x = 8, which is visible in the bounds at the 1e-13 level.
+__device__ double bessel_j1(double x) {
+  const double ax = fabs(x);
+  const double sg = x < 0 ? -1.0 : 1.0;
+  if (ax <= 8.0) return j1(x);
+  if (ax < 20.0) {
+    int n0 = static_cast<int>(ax) + 40;
+    n0 += n0 & 1;                       // even start
+    double jp1 = 0.0, jn = 1e-30, sum = 2.0 * jn, j1v = 0.0;
+    for (int n = n0; n >= 1; --n) {
+      const double jm1 = (2.0 * n / ax) * jn - jp1;   // J_{n-1}
+      jp1 = jn;
+      jn = jm1;
+      const int m = n - 1;
+      if (m == 1) j1v = jn;
+      if ((m & 1) == 0) sum += (m == 0 ? 1.0 : 2.0) * jn;
+      if (fabs(jn) > 1e200) {          // rescale to stay in range
+        jn *= 1e-200;
+        jp1 *= 1e-200;
+        sum *= 1e-200;
+        j1v *= 1e-200;
+      }
+    }
+    return sg * j1v / sum;
+  }
+  const double inv = 1.0 / ax;
+  double P = 1.0, Q = 0.0;
+  double a = 1.0;                        // a_m x^{-m} with alternating signs folded in below
+  for (int m = 1; m < 60; ++m) {
+    a *= (4.0 - (2.0 * m - 1.0) * (2.0 * m - 1.0)) / (8.0 * m) * inv;
+    // m odd -> Q term (-1)^((m-1)/2), m even -> P term (-1)^(m/2)
+    const int k = m >> 1;
+    const double term = ((k & 1) ? -a : a);
+    if (m & 1) Q += term;
+    else P += term;
+    if (fabs(a) < 1e-18) break;
+  }
+  double s, c;
+  sincos(ax, &s, &c);
+  const double r2 = 0.70710678118654752440084436210485;   // 1/sqrt(2)
+  const double cchi = (s - c) * r2;       // cos(x - 3 pi / 4)
+  const double schi = -(s + c) * r2;      // sin(x - 3 pi / 4)
+  return sg * sqrt(2.0 / (kPi * ax)) * (P * cchi - Q * schi);
+}
+
 __device__ double shape_coeff(const Incl& in, int d, const int n[3]) {
   if (in.shape == GHB_BOX) {
     double v = 1.0;
@@ -139,7 +195,7 @@ __device__ double shape_coeff(const Incl& in, int d, const int n[3]) {
   const double rho = sqrt(rho2);
   if (in.shape == GHB_DISK) {
     if (rho2 == 0.0) return kPi * r * r;
-    return r * j1(2.0 * kPi * r * rho) / rho;
+    return r * bessel_j1(2.0 * kPi * r * rho) / rho;
   }
   // sphere
   const double q = 2.0 * kPi * r * rho;
@@ -217,87 +273,103 @@ __global__ void rhs_kernel(double2* b, const double2* tab, Geometry g, FieldGeom
   }
 }
 
-// y = G w (with the Hermitian part taken on k_d = 0); y must not alias w.
+// ---------------------------------------------------------------------------
+// CG vector operations on one operand (CgItem), executed by blocks
+// bid = 0..nb-1; used by one-operand launches and by batched launches over
+// many operands alike.
+// ---------------------------------------------------------------------------
+#define GHB_FIELD_LOOP(e, fg, bid, nb)                                                  \
+  for (int64_t e = (bid) * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < (fg).P; \
+       e += (nb) * static_cast<int64_t>(blockDim.x))
+
+// q = G w (with the Hermitian part taken on k_d = 0); q must not alias w.
 template <typename T>
-__global__ void project_kernel(typename CT<T>::type* y, const typename CT<T>::type* w, FieldGeom fg,
-                               int kind) {
+__device__ void op_project(const CgItem& it, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const FieldGeom& fg = it.fg;
+  const C* w = static_cast<const C*>(it.w);
+  C* y = static_cast<C*>(it.q);
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
     int k[3];
     int j;
     kvec(fg, e, k, j);
-    const int64_t em = mirror_index(fg, e, j);
+    const int64_t em = mirror_index(fg, k, j);
     C wv[3], q[3];
     for (int c = 0; c < fg.d; ++c) wv[c] = hermitian_part(w, fg.P, c, e, em);
-    project_vec<T>(fg.d, k, kind, wv, q);
+    project_vec<T>(fg.d, k, it.kind, wv, q);
     for (int c = 0; c < fg.d; ++c) y[c * fg.P + e] = q[c];
   }
 }
 
+// x = 0, r = b, p = 0, <b, b>; the last block initialises the CG scalars.
 template <typename T>
-__global__ void cg_init_kernel(typename CT<T>::type* x, typename CT<T>::type* r,
-                               typename CT<T>::type* p, const typename CT<T>::type* b, FieldGeom fg,
-                               CgState* st, double* partials, double tol, int maxiter) {
+__device__ void op_init(const CgItem& it, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
-  double acc = 0.0;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    int k[3];
-    int j;
-    kvec(fg, e, k, j);
-    const double wt = (j == 0) ? 1.0 : 2.0;
+  const FieldGeom& fg = it.fg;
+  C* x = static_cast<C*>(it.x);
+  C* r = static_cast<C*>(it.r);
+  C* p = static_cast<C*>(it.p);
+  const C* b = static_cast<const C*>(it.b);
+  CgState* st = it.st;
+  // per-thread partial sums in the field's precision (a few dozen terms), the
+  // cross-thread and cross-block sums in FP64
+  T acc = T(0);
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
+    const int j = static_cast<int>(static_cast<unsigned>(e) % static_cast<unsigned>(fg.h));
+    const T wt = (j == 0) ? T(1) : T(2);
     for (int c = 0; c < fg.d; ++c) {
       const int64_t i = c * fg.P + e;
       const C bv = b[i];
       x[i] = mk(T(0), T(0));
       p[i] = mk(T(0), T(0));
       r[i] = bv;
-      acc += wt * (double(bv.x) * bv.x + double(bv.y) * bv.y);
+      acc += wt * (bv.x * bv.x + bv.y * bv.y);
     }
   }
   double tot;
-  if (grid_sum_last(acc, partials, &st->ticket, &tot)) {
+  if (grid_sum_last(static_cast<double>(acc), it.partials, &st->ticket, &tot, bid, nb)) {
     st->bb = tot;
     st->rr = tot;
-    st->tol2 = tol * tol * tot;
+    st->tol2 = it.tol * it.tol * tot;
     st->alpha = 0.0;
     st->beta = 0.0;
     st->pq = 0.0;
     st->iter = 0;
-    st->maxiter = maxiter;
+    st->maxiter = it.maxiter;
     st->done = (tot == 0.0) ? CONVERGED : RUNNING;
   }
 }
 
 // q = G w, <p, q>; the last block forms alpha = <r, r> / <p, A p>.
 template <typename T>
-__global__ void project_dot_kernel(typename CT<T>::type* q, const typename CT<T>::type* w,
-                                   const typename CT<T>::type* p, FieldGeom fg, int kind,
-                                   CgState* st, double* partials) {
+__device__ void op_project_dot(const CgItem& it, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
+  const FieldGeom& fg = it.fg;
+  CgState* st = it.st;
   if (st->done != RUNNING) return;
-  double acc = 0.0;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  C* q = static_cast<C*>(it.q);
+  const C* w = static_cast<const C*>(it.w);
+  const C* p = static_cast<const C*>(it.p);
+  T acc = T(0);   // per-thread partial in the field's precision, FP64 across threads
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
     int k[3];
     int j;
     kvec(fg, e, k, j);
-    const double wt = (j == 0) ? 1.0 : 2.0;
-    const int64_t em = mirror_index(fg, e, j);
+    const T wt = (j == 0) ? T(1) : T(2);
+    const int64_t em = mirror_index(fg, k, j);
     C wv[3], qv[3];
     for (int c = 0; c < fg.d; ++c) wv[c] = hermitian_part(w, fg.P, c, e, em);
-    project_vec<T>(fg.d, k, kind, wv, qv);
-    double s = 0.0;
+    project_vec<T>(fg.d, k, it.kind, wv, qv);
+    T sacc = T(0);
     for (int c = 0; c < fg.d; ++c) {
       q[c * fg.P + e] = qv[c];
       const C pv = p[c * fg.P + e];
-      s += double(pv.x) * qv[c].x + double(pv.y) * qv[c].y;
+      sacc += pv.x * qv[c].x + pv.y * qv[c].y;
     }
-    acc += wt * s;
+    acc += wt * sacc;
   }
   double tot;
-  if (grid_sum_last(acc, partials, &st->ticket, &tot)) {
+  if (grid_sum_last(static_cast<double>(acc), it.partials, &st->ticket, &tot, bid, nb)) {
     st->pq = tot;
     if (!(tot > 0.0) || !isfinite(tot)) {
       st->done = BREAKDOWN;
@@ -310,19 +382,20 @@ __global__ void project_dot_kernel(typename CT<T>::type* q, const typename CT<T>
 
 // x += alpha p, r -= alpha q, <r, r>; the last block forms beta and the stop test.
 template <typename T>
-__global__ void update_kernel(typename CT<T>::type* x, typename CT<T>::type* r,
-                              const typename CT<T>::type* p, const typename CT<T>::type* q,
-                              FieldGeom fg, CgState* st, double* partials) {
+__device__ void op_update(const CgItem& it, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
+  const FieldGeom& fg = it.fg;
+  CgState* st = it.st;
   if (st->done != RUNNING) return;
+  C* x = static_cast<C*>(it.x);
+  C* r = static_cast<C*>(it.r);
+  const C* p = static_cast<const C*>(it.p);
+  const C* q = static_cast<const C*>(it.q);
   const T al = static_cast<T>(st->alpha);
-  double acc = 0.0;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i1 = (fg.d == 2) ? e / fg.h : e / (static_cast<int64_t>(fg.N[1]) * fg.h);
-    (void)i1;
-    const int j = static_cast<int>(e % fg.h);
-    const double wt = (j == 0) ? 1.0 : 2.0;
+  T acc = T(0);   // per-thread partial in the field's precision, FP64 across threads
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
+    const int j = static_cast<int>(static_cast<unsigned>(e) % static_cast<unsigned>(fg.h));
+    const T wt = (j == 0) ? T(1) : T(2);
     for (int c = 0; c < fg.d; ++c) {
       const int64_t i = c * fg.P + e;
       const C pv = p[i], qv = q[i];
@@ -331,11 +404,11 @@ __global__ void update_kernel(typename CT<T>::type* x, typename CT<T>::type* r,
       rv = mk(rv.x - al * qv.x, rv.y - al * qv.y);
       x[i] = xv;
       r[i] = rv;
-      acc += wt * (double(rv.x) * rv.x + double(rv.y) * rv.y);
+      acc += wt * (rv.x * rv.x + rv.y * rv.y);
     }
   }
   double tot;
-  if (grid_sum_last(acc, partials, &st->ticket, &tot)) {
+  if (grid_sum_last(static_cast<double>(acc), it.partials, &st->ticket, &tot, bid, nb)) {
     const double rr_old = st->rr;
     st->beta = tot / rr_old;
     st->rr = tot;
@@ -346,12 +419,15 @@ __global__ void update_kernel(typename CT<T>::type* x, typename CT<T>::type* r,
   }
 }
 
-__global__ void residual_kernel(double2* r, const double2* b, const double2* y, FieldGeom fg,
-                                CgState* st, double* partials) {
+// FP64 residual r = b - w and <r, r> into st->rr.
+__device__ void op_residual(const CgItem& it, int64_t bid, int64_t nb) {
+  const FieldGeom& fg = it.fg;
+  double2* r = static_cast<double2*>(it.r);
+  const double2* b = static_cast<const double2*>(it.b);
+  const double2* y = static_cast<const double2*>(it.w);
   double acc = 0.0;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int j = static_cast<int>(e % fg.h);
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
+    const int j = static_cast<int>(static_cast<unsigned>(e) % static_cast<unsigned>(fg.h));
     const double wt = (j == 0) ? 1.0 : 2.0;
     for (int c = 0; c < fg.d; ++c) {
       const int64_t i = c * fg.P + e;
@@ -361,19 +437,70 @@ __global__ void residual_kernel(double2* r, const double2* b, const double2* y, 
     }
   }
   double tot;
-  if (grid_sum_last(acc, partials, &st->ticket, &tot)) st->rr = tot;
+  if (grid_sum_last(acc, it.partials, &it.st->ticket, &tot, bid, nb)) it.st->rr = tot;
 }
 
-__global__ void to_f32_kernel(float2* dst, const double2* src, int64_t n) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    dst[i] = make_float2(static_cast<float>(src[i].x), static_cast<float>(src[i].y));
+// FP32 copy q = (float) w of an FP64 field.
+__device__ void op_to_f32(const CgItem& it, int64_t bid, int64_t nb) {
+  const FieldGeom& fg = it.fg;
+  float2* dst = static_cast<float2*>(it.q);
+  const double2* src = static_cast<const double2*>(it.w);
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
+    for (int c = 0; c < fg.d; ++c) {
+      const int64_t i = c * fg.P + e;
+      dst[i] = make_float2(static_cast<float>(src[i].x), static_cast<float>(src[i].y));
+    }
+  }
 }
 
-__global__ void accum_f32_kernel(double2* x, const float2* dx, int64_t n) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    x[i] = make_double2(x[i].x + static_cast<double>(dx[i].x), x[i].y + static_cast<double>(dx[i].y));
+// FP64 accumulation x = w + (double) p with p an FP32 correction.
+__device__ void op_accum(const CgItem& it, int64_t bid, int64_t nb) {
+  const FieldGeom& fg = it.fg;
+  double2* x = static_cast<double2*>(it.x);
+  const double2* w = static_cast<const double2*>(it.w);
+  const float2* dx = static_cast<const float2*>(it.p);
+  GHB_FIELD_LOOP(e, fg, bid, nb) {
+    for (int c = 0; c < fg.d; ++c) {
+      const int64_t i = c * fg.P + e;
+      x[i] = make_double2(w[i].x + static_cast<double>(dx[i].x), w[i].y + static_cast<double>(dx[i].y));
+    }
+  }
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ void run_op(const CgItem& it, int64_t bid, int64_t nb) {
+  if constexpr (OP == CG_INIT) op_init<T>(it, bid, nb);
+  else if constexpr (OP == CG_PROJECT_DOT) op_project_dot<T>(it, bid, nb);
+  else if constexpr (OP == CG_UPDATE) op_update<T>(it, bid, nb);
+  else if constexpr (OP == CG_PROJECT) op_project<T>(it, bid, nb);
+  else if constexpr (OP == CG_RESIDUAL) op_residual(it, bid, nb);
+  else if constexpr (OP == CG_TO_F32) op_to_f32(it, bid, nb);
+  else if constexpr (OP == CG_ACCUM) op_accum(it, bid, nb);
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kFieldThreads) cg_kernel(CgItem it) {
+  run_op<T, OP>(it, blockIdx.x, gridDim.x);
+}
+
+template <typename Item>
+__device__ __forceinline__ int find_cg_item(const Item* items, int n, int64_t b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].block_begin <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kFieldThreads) cg_kernel_batch(const CgItem* __restrict__ items, int n) {
+  __shared__ int s_item;
+  if (threadIdx.x == 0) s_item = find_cg_item(items, n, blockIdx.x);
+  __syncthreads();
+  const CgItem& it = items[s_item];
+  run_op<T, OP>(it, blockIdx.x - it.block_begin, it.nblocks);
 }
 
 __global__ void to_f32_real_kernel(float* dst, const double* src, int64_t n) {
@@ -420,13 +547,30 @@ ghb_status launch_rhs(void* b, const double2* tab, const Geometry& g, const doub
 template ghb_status launch_rhs<double>(void*, const double2*, const Geometry&, const double*, int,
                                        cudaStream_t);
 
-template <typename T>
-ghb_status launch_project(void* y, const void* w, const FieldGeom& fg, int kind, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  project_kernel<T><<<field_grid(fg.P), kFieldThreads, 0, s>>>(static_cast<C*>(y),
-                                                                static_cast<const C*>(w), fg, kind);
+namespace {
+template <typename T, int OP>
+ghb_status launch_one(const CgItem& it, cudaStream_t s) {
+  cg_kernel<T, OP><<<static_cast<unsigned>(it.nblocks), kFieldThreads, 0, s>>>(it);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
+}
+CgItem make_item(const FieldGeom& fg) {
+  CgItem it{};
+  it.fg = fg;
+  it.nblocks = field_grid(fg.P);
+  return it;
+}
+}  // namespace
+
+int64_t cg_blocks(const FieldGeom& fg) { return field_grid(fg.P); }
+
+template <typename T>
+ghb_status launch_project(void* y, const void* w, const FieldGeom& fg, int kind, cudaStream_t s) {
+  CgItem it = make_item(fg);
+  it.q = y;
+  it.w = w;
+  it.kind = kind;
+  return launch_one<T, CG_PROJECT>(it, s);
 }
 template ghb_status launch_project<double>(void*, const void*, const FieldGeom&, int, cudaStream_t);
 template ghb_status launch_project<float>(void*, const void*, const FieldGeom&, int, cudaStream_t);
@@ -434,12 +578,16 @@ template ghb_status launch_project<float>(void*, const void*, const FieldGeom&, 
 template <typename T>
 ghb_status launch_cg_init(void* x, void* r, void* p, const void* b, const FieldGeom& fg, CgState* st,
                           double* partials, double tol, int maxiter, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  cg_init_kernel<T><<<field_grid(fg.P), kFieldThreads, 0, s>>>(
-      static_cast<C*>(x), static_cast<C*>(r), static_cast<C*>(p), static_cast<const C*>(b), fg, st,
-      partials, tol, maxiter);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
+  CgItem it = make_item(fg);
+  it.x = x;
+  it.r = r;
+  it.p = p;
+  it.b = b;
+  it.st = st;
+  it.partials = partials;
+  it.tol = tol;
+  it.maxiter = maxiter;
+  return launch_one<T, CG_INIT>(it, s);
 }
 template ghb_status launch_cg_init<double>(void*, void*, void*, const void*, const FieldGeom&,
                                            CgState*, double*, double, int, cudaStream_t);
@@ -449,11 +597,14 @@ template ghb_status launch_cg_init<float>(void*, void*, void*, const void*, cons
 template <typename T>
 ghb_status launch_project_dot(void* q, const void* w, const void* p, const FieldGeom& fg, int kind,
                               CgState* st, double* partials, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  project_dot_kernel<T><<<field_grid(fg.P), kFieldThreads, 0, s>>>(
-      static_cast<C*>(q), static_cast<const C*>(w), static_cast<const C*>(p), fg, kind, st, partials);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
+  CgItem it = make_item(fg);
+  it.q = q;
+  it.w = w;
+  it.p = const_cast<void*>(p);
+  it.kind = kind;
+  it.st = st;
+  it.partials = partials;
+  return launch_one<T, CG_PROJECT_DOT>(it, s);
 }
 template ghb_status launch_project_dot<double>(void*, const void*, const void*, const FieldGeom&,
                                                int, CgState*, double*, cudaStream_t);
@@ -463,12 +614,14 @@ template ghb_status launch_project_dot<float>(void*, const void*, const void*, c
 template <typename T>
 ghb_status launch_update(void* x, void* r, const void* p, const void* q, const FieldGeom& fg,
                          CgState* st, double* partials, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  update_kernel<T><<<field_grid(fg.P), kFieldThreads, 0, s>>>(
-      static_cast<C*>(x), static_cast<C*>(r), static_cast<const C*>(p), static_cast<const C*>(q), fg,
-      st, partials);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
+  CgItem it = make_item(fg);
+  it.x = x;
+  it.r = r;
+  it.p = const_cast<void*>(p);
+  it.q = const_cast<void*>(q);
+  it.st = st;
+  it.partials = partials;
+  return launch_one<T, CG_UPDATE>(it, s);
 }
 template ghb_status launch_update<double>(void*, void*, const void*, const void*, const FieldGeom&,
                                           CgState*, double*, cudaStream_t);
@@ -477,22 +630,49 @@ template ghb_status launch_update<float>(void*, void*, const void*, const void*,
 
 ghb_status launch_residual(double2* r, const double2* b, const double2* y, const FieldGeom& fg,
                            CgState* st, double* partials, cudaStream_t s) {
-  residual_kernel<<<field_grid(fg.P), kFieldThreads, 0, s>>>(r, b, y, fg, st, partials);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
+  CgItem it = make_item(fg);
+  it.r = r;
+  it.b = b;
+  it.w = y;
+  it.st = st;
+  it.partials = partials;
+  return launch_one<double, CG_RESIDUAL>(it, s);
 }
 
-ghb_status launch_to_f32(float2* dst, const double2* src, int64_t n, cudaStream_t s) {
-  to_f32_kernel<<<field_grid(n), kFieldThreads, 0, s>>>(dst, src, n);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
+ghb_status launch_to_f32(float2* dst, const double2* src, const FieldGeom& fg, cudaStream_t s) {
+  CgItem it = make_item(fg);
+  it.q = dst;
+  it.w = src;
+  return launch_one<double, CG_TO_F32>(it, s);
 }
 
-ghb_status launch_accum_f32(double2* x, const float2* dx, int64_t n, cudaStream_t s) {
-  accum_f32_kernel<<<field_grid(n), kFieldThreads, 0, s>>>(x, dx, n);
+ghb_status launch_accum_f32(double2* x, const double2* base, const float2* dx, const FieldGeom& fg,
+                            cudaStream_t s) {
+  CgItem it = make_item(fg);
+  it.x = x;
+  it.w = base;
+  it.p = const_cast<float2*>(dx);
+  return launch_one<double, CG_ACCUM>(it, s);
+}
+
+template <typename T>
+ghb_status launch_cg_batch(int op, const CgItem* items, int n, int64_t blocks, cudaStream_t s) {
+  const unsigned g = static_cast<unsigned>(blocks);
+  switch (op) {
+    case CG_INIT: cg_kernel_batch<T, CG_INIT><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    case CG_PROJECT_DOT: cg_kernel_batch<T, CG_PROJECT_DOT><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    case CG_UPDATE: cg_kernel_batch<T, CG_UPDATE><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    case CG_PROJECT: cg_kernel_batch<T, CG_PROJECT><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    case CG_RESIDUAL: cg_kernel_batch<double, CG_RESIDUAL><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    case CG_TO_F32: cg_kernel_batch<double, CG_TO_F32><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    case CG_ACCUM: cg_kernel_batch<double, CG_ACCUM><<<g, kFieldThreads, 0, s>>>(items, n); break;
+    default: set_error("internal: bad batched CG op"); return GHB_ERR_INVALID;
+  }
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }
+template ghb_status launch_cg_batch<double>(int, const CgItem*, int, int64_t, cudaStream_t);
+template ghb_status launch_cg_batch<float>(int, const CgItem*, int, int64_t, cudaStream_t);
 
 ghb_status launch_to_f32_real(float* dst, const double* src, int64_t n, cudaStream_t s) {
   to_f32_real_kernel<<<field_grid(n), kFieldThreads, 0, s>>>(dst, src, n);

@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "fft.cuh"
-#include "../../include/ghb.h"
+#include "ghb.h"
 
 namespace ghb {
 
@@ -82,6 +82,8 @@ struct PlanHolder {
   int* d_perm = nullptr;
   double2* d_tw64 = nullptr;
   float2* d_tw32 = nullptr;
+  double2* d_roots64 = nullptr;
+  float2* d_roots32 = nullptr;
 };
 
 ghb_status make_plan(int M, PlanHolder& out);
@@ -135,6 +137,34 @@ struct RowArgs {
 template <typename T>
 ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_t s);
 
+// Work items of batched launches: every item is one operand (an instance's
+// solve) with its own sizes and plan; it owns blocks [block_begin, block_begin + nblocks).
+struct ColItem {
+  ColArgs a;
+  const FftPlan* pl;     // device copy of the item's plan
+  int64_t block_begin;
+};
+
+struct RowItem {
+  RowArgs a;
+  const FftPlan* pl;
+  int rows_per_cta;
+  int pad;
+  int64_t nblocks;
+  int64_t block_begin;
+};
+
+// Batched launches; TW / NL and the shared-memory size are chosen by the caller
+// for the largest M of the batch (col_tile_width, row_lines).
+template <typename T>
+ghb_status launch_col_batch(int sign, int mode, int TW, const ColItem* items, int n, int64_t blocks,
+                            size_t smem, cudaStream_t s);
+template <typename T>
+ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem,
+                            cudaStream_t s);
+// rows per CTA and interleaved complex lines of a row pass
+void row_lines(int mode, int nfields, int ncomp, int* rows_per_cta, int* NL);
+
 // Field-level kernels (half-spectrum fields of one context).
 struct FieldGeom {
   int d;
@@ -162,8 +192,33 @@ ghb_status launch_update(void* x, void* r, const void* p, const void* q, const F
 // r64 = b64 - y64, rr into st (FP64 outer residual); also st->done reset
 ghb_status launch_residual(double2* r, const double2* b, const double2* y, const FieldGeom& fg,
                            CgState* st, double* partials, cudaStream_t s);
-ghb_status launch_to_f32(float2* dst, const double2* src, int64_t n, cudaStream_t s);
-ghb_status launch_accum_f32(double2* x, const float2* dx, int64_t n, cudaStream_t s);
+ghb_status launch_to_f32(float2* dst, const double2* src, const FieldGeom& fg, cudaStream_t s);
+// x = base + (double) dx
+ghb_status launch_accum_f32(double2* x, const double2* base, const float2* dx, const FieldGeom& fg,
+                            cudaStream_t s);
+
+// CG vector operations over many operands in one launch.
+enum CgOp { CG_INIT = 0, CG_PROJECT_DOT, CG_UPDATE, CG_PROJECT, CG_RESIDUAL, CG_TO_F32, CG_ACCUM };
+struct CgItem {
+  FieldGeom fg;
+  void* x;
+  void* r;
+  void* p;
+  void* q;
+  const void* w;
+  const void* b;
+  CgState* st;
+  double* partials;   // at least nblocks doubles
+  int kind;
+  int maxiter;
+  double tol;
+  int64_t nblocks;
+  int64_t block_begin;
+};
+// blocks a one-operand launch of the CG vector operations uses for this field
+int64_t cg_blocks(const FieldGeom& fg);
+template <typename T>
+ghb_status launch_cg_batch(int op, const CgItem* items, int n, int64_t blocks, cudaStream_t s);
 ghb_status launch_to_f32_real(float* dst, const double* src, int64_t n, cudaStream_t s);
 ghb_status launch_add_constant(double2* v, const double2* e, const FieldGeom& fg, const double* E,
                                cudaStream_t s);

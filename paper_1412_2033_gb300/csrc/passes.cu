@@ -13,91 +13,15 @@
 //                     ENERGY: accumulate the Gram sums
 //                             (1/|M|) sum_m A_M(x_m) v_i(x_m).v_j(x_m).
 //                   Two real lines share one complex transform (z = u + i v).
+#include <cmath>
+
 #include "ghb_internal.cuh"
-#include "reduce.cuh"
 
 namespace ghb {
 
-// ---------------------------------------------------------------------------
-// column pass
-// ---------------------------------------------------------------------------
-template <typename T, int TW, int SIGN, int MODE>
-__global__ void __launch_bounds__(512) col_kernel(ColArgs a, FftPlan pl) {
-  using C = typename CT<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  __shared__ StageSmem st;
-  if (a.st != nullptr && a.st->done != RUNNING) return;
-  load_stages(st, pl);
-
-  const int M = pl.M;
-  const int64_t tiles = (a.inner + TW - 1) / TW;
-  const int64_t o = blockIdx.x / tiles;
-  const int64_t j0 = (blockIdx.x % tiles) * TW;
-  const int width = static_cast<int>(a.inner - j0 < TW ? a.inner - j0 : TW);
-  const C* __restrict__ tw = twtab<C>(pl);
-  const int* __restrict__ perm = pl.perm;
-
-  if (SIGN > 0) {
-    for (int u = threadIdx.x; u < M * TW; u += blockDim.x) buf[u] = mk(T(0), T(0));
-    __syncthreads();
-    const C* __restrict__ in = static_cast<const C*>(a.in);
-    const int Lin = a.Lin;
-    const int half = (Lin - 1) / 2;
-    T beta = T(0);
-    if (MODE == COL_PUPDATE) beta = static_cast<T>(a.st->beta);
-    for (int u = threadIdx.x; u < Lin * TW; u += blockDim.x) {
-      const int t = u % TW;
-      const int i = u / TW;
-      if (t < width) {
-        const int64_t idx = (o * Lin + i) * a.inner + j0 + t;
-        C v = in[idx];
-        if (MODE == COL_PUPDATE) {
-          C po = static_cast<const C*>(a.pold)[idx];
-          v = mk(v.x + beta * po.x, v.y + beta * po.y);
-          static_cast<C*>(a.pnew)[idx] = v;
-        }
-        int k = i - half;
-        if (k < 0) k += M;
-        buf[__ldg(&perm[k]) * TW + t] = v;
-      }
-    }
-    __syncthreads();
-    fft_dit<+1, TW>(buf, st, pl.nst, M, tw);
-    C* __restrict__ out = static_cast<C*>(a.out);
-    for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
-      const int t = u % TW;
-      const int m = u / TW;
-      if (t < width) out[(o * M + m) * a.inner + j0 + t] = buf[m * TW + t];
-    }
-  } else {
-    const C* __restrict__ in = static_cast<const C*>(a.in);
-    for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
-      const int t = u % TW;
-      const int m = u / TW;
-      buf[u] = (t < width) ? in[(o * M + m) * a.inner + j0 + t] : mk(T(0), T(0));
-    }
-    __syncthreads();
-    fft_dif<-1, TW>(buf, st, pl.nst, M, tw);
-    C* __restrict__ out = static_cast<C*>(a.out);
-    const int Lout = a.Lout;
-    const int half = (Lout - 1) / 2;
-    const T inv = T(1) / T(M);
-    for (int u = threadIdx.x; u < Lout * TW; u += blockDim.x) {
-      const int t = u % TW;
-      const int i = u / TW;
-      if (t < width) {
-        int k = i - half;
-        if (k < 0) k += M;
-        C v = buf[__ldg(&perm[k]) * TW + t];
-        out[(o * Lout + i) * a.inner + j0 + t] = inv * v;
-      }
-    }
-  }
-}
-
 size_t col_smem_bytes(int M, int TW, int elem_bytes) {
-  return static_cast<size_t>(M) * TW * elem_bytes;
+  return elem_bytes == 8 ? padded_elems<float2>(static_cast<size_t>(M) * TW) * 8
+                         : padded_elems<double2>(static_cast<size_t>(M) * TW) * 16;
 }
 
 // Widest tile that keeps two CTAs per SM (<= ~110 KB of shared memory).
@@ -109,23 +33,16 @@ int col_tile_width(int M, int elem_bytes) {
   return 1;
 }
 
-template <typename T, int TW, int SIGN, int MODE>
-static ghb_status launch_col_t(const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  const size_t smem = col_smem_bytes(pl.M, TW, sizeof(C));
-  static bool attr_set = false;
-  if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(col_kernel<T, TW, SIGN, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr_set = true;
-  }
-  const int64_t tiles = (a.inner + TW - 1) / TW;
-  const int64_t grid = tiles * a.outer;
-  const int threads = (pl.M * TW >= 2048) ? 512 : 256;
-  col_kernel<T, TW, SIGN, MODE><<<static_cast<unsigned>(grid), threads, smem, s>>>(a, pl);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
-}
+// Launchers defined by instantiation in the col_*.cu / row_*.cu units.
+template <typename T, int TW>
+ghb_status launch_col_tw(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
+template <typename T, int NL, int MODE>
+ghb_status launch_row_nl(const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
+template <typename T, int TW>
+ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, int64_t blocks, size_t smem,
+                               cudaStream_t s);
+template <typename T, int NL, int MODE>
+ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size_t smem, cudaStream_t s);
 
 template <typename T>
 ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
@@ -135,21 +52,14 @@ ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, c
     set_error("transform length too large for one CTA: M=" + std::to_string(pl.M));
     return GHB_ERR_INVALID;
   }
-#define GHB_COL_CASE(W)                                                              \
-  case W:                                                                            \
-    if (sign > 0)                                                                    \
-      return mode == COL_PUPDATE ? launch_col_t<T, W, +1, COL_PUPDATE>(a, pl, s)     \
-                                 : launch_col_t<T, W, +1, COL_PLAIN>(a, pl, s);      \
-    return launch_col_t<T, W, -1, COL_PLAIN>(a, pl, s);
   switch (TW) {
-    GHB_COL_CASE(1)
-    GHB_COL_CASE(2)
-    GHB_COL_CASE(4)
-    GHB_COL_CASE(8)
-    GHB_COL_CASE(16)
+    case 1: return launch_col_tw<T, 1>(sign, mode, a, pl, s);
+    case 2: return launch_col_tw<T, 2>(sign, mode, a, pl, s);
+    case 4: return launch_col_tw<T, 4>(sign, mode, a, pl, s);
+    case 8: return launch_col_tw<T, 8>(sign, mode, a, pl, s);
+    case 16: return launch_col_tw<T, 16>(sign, mode, a, pl, s);
     default: break;
   }
-#undef GHB_COL_CASE
   set_error("internal: bad tile width");
   return GHB_ERR_INVALID;
 }
@@ -157,210 +67,78 @@ ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, c
 template ghb_status launch_col<double>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 template ghb_status launch_col<float>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// row pass
-// ---------------------------------------------------------------------------
-struct LineDesc {
-  int64_t row;
-  int field;
-  int comp;
-  int valid;
-};
-
-template <typename T, int NL, int MODE>
-__global__ void __launch_bounds__(256) row_kernel(RowArgs a, FftPlan pl, int rows_per_cta) {
-  using C = typename CT<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  __shared__ StageSmem st;
-  __shared__ LineDesc ld[2 * NL];
-  __shared__ double red[32];
-  __shared__ bool last;
-  if (a.st != nullptr && a.st->done != RUNNING) return;
-  load_stages(st, pl);
-
-  const int M = pl.M;
-  const int H = a.H;
-  const int per_row = a.nfields * a.ncomp;
-  const int nrl = rows_per_cta * per_row;   // real lines per row group
-  const int64_t groups = (a.rows + rows_per_cta - 1) / rows_per_cta;
-  const C* __restrict__ tw = twtab<C>(pl);
-  const int* __restrict__ perm = pl.perm;
-  double g[6] = {0, 0, 0, 0, 0, 0};       // ENERGY: upper triangle of F x F, F <= 3
-
-  for (int64_t grp = blockIdx.x; grp < groups; grp += gridDim.x) {
-    const int64_t row0 = grp * rows_per_cta;
-    if (threadIdx.x < 2 * NL) {
-      const int rho = threadIdx.x;
-      LineDesc d;
-      d.row = row0 + rho / per_row;
-      d.field = (rho / a.ncomp) % a.nfields;
-      d.comp = rho % a.ncomp;
-      d.valid = (rho < nrl) && (d.row < a.rows);
-      ld[rho] = d;
-    }
-    for (int u = threadIdx.x; u < M * NL; u += blockDim.x) buf[u] = mk(T(0), T(0));
-    __syncthreads();
-
-    // Hermitian completion of each pair of half spectra: Z(k) = X0(k) + i X1(k),
-    // Z(-k) = conj X0(k) + i conj X1(k); scattered to digit-reversed positions.
-    for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
-      const int j = (NL == 1) ? 0 : u % NL;
-      const int k = (NL == 1) ? u : u / NL;
-      const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
-      C A = mk(T(0), T(0)), B = mk(T(0), T(0));
-      if (d0.valid)
-        A = static_cast<const C*>(a.t[d0.field])[d0.comp * a.comp_stride + d0.row * H + k];
-      if (d1.valid)
-        B = static_cast<const C*>(a.t[d1.field])[d1.comp * a.comp_stride + d1.row * H + k];
-      buf[__ldg(&perm[k]) * NL + j] = mk(A.x - B.y, A.y + B.x);
-      if (k > 0) buf[__ldg(&perm[M - k]) * NL + j] = mk(A.x + B.y, B.x - A.y);
-    }
-    __syncthreads();
-    fft_dit<+1, NL>(buf, st, pl.nst, M, tw);
-
-    if (MODE == ROW_MATVEC) {
-      const T* __restrict__ am = static_cast<const T*>(a.a);
-      for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
-        const int j = (NL == 1) ? 0 : u % NL;
-        const int m = (NL == 1) ? u : u / NL;
-        const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
-        C z = buf[m * NL + j];
-        const T a0 = d0.valid ? am[d0.row * M + m] : T(0);
-        const T a1 = d1.valid ? am[d1.row * M + m] : T(0);
-        buf[m * NL + j] = mk(a0 * z.x, a1 * z.y);
-      }
-      __syncthreads();
-      fft_dif<-1, NL>(buf, st, pl.nst, M, tw);
-      const T sc = T(0.5) / T(M);
-      for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
-        const int j = (NL == 1) ? 0 : u % NL;
-        const int k = (NL == 1) ? u : u / NL;
-        const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
-        const C W = buf[__ldg(&perm[k]) * NL + j];
-        const C Wm = buf[__ldg(&perm[k == 0 ? 0 : M - k]) * NL + j];
-        if (d0.valid)
-          static_cast<C*>(a.t[d0.field])[d0.comp * a.comp_stride + d0.row * H + k] =
-              mk(sc * (W.x + Wm.x), sc * (W.y - Wm.y));
-        if (d1.valid)
-          static_cast<C*>(a.t[d1.field])[d1.comp * a.comp_stride + d1.row * H + k] =
-              mk(sc * (W.y + Wm.y), sc * (Wm.x - W.x));
-      }
-    } else if (MODE == ROW_TOREAL) {
-      T* __restrict__ out = static_cast<T*>(a.out_real);
-      for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
-        const int j = (NL == 1) ? 0 : u % NL;
-        const int m = (NL == 1) ? u : u / NL;
-        const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
-        const C z = buf[m * NL + j];
-        if (d0.valid) out[d0.row * M + m] = z.x;
-        if (d1.valid) out[d1.row * M + m] = z.y;
-      }
-    } else {  // ROW_ENERGY: one row per group, lines ordered (field, comp)
-      const T* __restrict__ am = static_cast<const T*>(a.a);
-      const int F = a.nfields, NC = a.ncomp;
-      const bool ok = ld[0].valid;
-      for (int m = threadIdx.x; ok && m < M; m += blockDim.x) {
-        const double am_ = static_cast<double>(am[ld[0].row * M + m]);
-        double u[10];
-#pragma unroll
-        for (int r = 0; r < 2 * NL; ++r) {
-          const C z = buf[m * NL + (r >> 1)];
-          u[r] = static_cast<double>((r & 1) ? z.y : z.x);
-        }
-        int e = 0;
-        for (int f = 0; f < F; ++f)
-          for (int h2 = f; h2 < F; ++h2, ++e) {
-            double s = 0.0;
-            for (int c = 0; c < NC; ++c) s += u[f * NC + c] * u[h2 * NC + c];
-            g[e] += am_ * s;
-          }
-      }
-    }
-    __syncthreads();
-  }
-
-  if (MODE == ROW_ENERGY) {
-    const int F = a.nfields;
-    const int ne = F * (F + 1) / 2;
-    for (int e = 0; e < ne; ++e) {
-      const double v = block_sum(g[e], red);
-      if (threadIdx.x == 0) a.partials[static_cast<int64_t>(blockIdx.x) * 6 + e] = v;
-    }
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned int t = atomicAdd(a.ticket, 1u);
-      last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      for (int e = 0; e < ne; ++e) {
-        double v = 0.0;
-        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-          v += __ldcg(&a.partials[static_cast<int64_t>(b) * 6 + e]);
-        v = block_sum(v, red);
-        if (threadIdx.x == 0) {
-          int ee = 0;
-          for (int f = 0; f < F; ++f)
-            for (int h2 = f; h2 < F; ++h2, ++ee)
-              if (ee == e) {
-                a.gram[f * F + h2] = v * a.scale;
-                a.gram[h2 * F + f] = v * a.scale;
-              }
-        }
-      }
-      if (threadIdx.x == 0) *a.ticket = 0u;
-    }
-  }
-}
-
-template <typename T, int NL, int MODE>
-static ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per_cta,
-                               cudaStream_t s) {
-  using C = typename CT<T>::type;
-  const size_t smem = static_cast<size_t>(pl.M) * NL * sizeof(C);
-  static bool attr_set = false;
-  if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(row_kernel<T, NL, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
-  if (smem > 200 * 1024) {
-    set_error("row transform too large for one CTA: M=" + std::to_string(pl.M));
-    return GHB_ERR_INVALID;
-  }
-  const int64_t groups = (a.rows + rows_per_cta - 1) / rows_per_cta;
-  int64_t grid = groups;
-  if (MODE == ROW_ENERGY && grid > 1024) grid = 1024;   // partials hold 1024 x 6 doubles
-  row_kernel<T, NL, MODE><<<static_cast<unsigned>(grid), 256, smem, s>>>(a, pl, rows_per_cta);
-  GHB_CUDA_TRY(cudaGetLastError());
-  return GHB_OK;
+void row_lines(int mode, int nfields, int ncomp, int* rows_per_cta, int* NL) {
+  const int per_row = nfields * ncomp;
+  int r = 1;
+  if (mode == ROW_MATVEC || mode == ROW_TOREAL) r = (per_row % 2 == 1) ? 2 : 1;
+  *rows_per_cta = r;
+  *NL = (r * per_row + 1) / 2;
 }
 
 template <typename T>
+ghb_status launch_col_batch(int sign, int mode, int TW, const ColItem* items, int n, int64_t blocks,
+                            size_t smem, cudaStream_t s) {
+  switch (TW) {
+    case 1: return launch_col_batch_tw<T, 1>(sign, mode, items, n, blocks, smem, s);
+    case 2: return launch_col_batch_tw<T, 2>(sign, mode, items, n, blocks, smem, s);
+    case 4: return launch_col_batch_tw<T, 4>(sign, mode, items, n, blocks, smem, s);
+    case 8: return launch_col_batch_tw<T, 8>(sign, mode, items, n, blocks, smem, s);
+    case 16: return launch_col_batch_tw<T, 16>(sign, mode, items, n, blocks, smem, s);
+    default: break;
+  }
+  set_error("internal: bad tile width");
+  return GHB_ERR_INVALID;
+}
+template ghb_status launch_col_batch<double>(int, int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_col_batch<float>(int, int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+
+template <typename T>
+ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem,
+                            cudaStream_t s) {
+  if (mode == ROW_MATVEC) {
+    if (NL == 1) return launch_row_batch_nl<T, 1, ROW_MATVEC>(items, n, blocks, smem, s);
+    if (NL == 3) return launch_row_batch_nl<T, 3, ROW_MATVEC>(items, n, blocks, smem, s);
+  } else if constexpr (sizeof(T) == 8) {
+    if (mode == ROW_TOREAL && NL == 1) return launch_row_batch_nl<T, 1, ROW_TOREAL>(items, n, blocks, smem, s);
+    if (mode == ROW_ENERGY) {
+      switch (NL) {
+        case 1: return launch_row_batch_nl<T, 1, ROW_ENERGY>(items, n, blocks, smem, s);
+        case 2: return launch_row_batch_nl<T, 2, ROW_ENERGY>(items, n, blocks, smem, s);
+        case 3: return launch_row_batch_nl<T, 3, ROW_ENERGY>(items, n, blocks, smem, s);
+        case 4: return launch_row_batch_nl<T, 4, ROW_ENERGY>(items, n, blocks, smem, s);
+        case 5: return launch_row_batch_nl<T, 5, ROW_ENERGY>(items, n, blocks, smem, s);
+        default: break;
+      }
+    }
+  }
+  set_error("internal: unsupported batched row pass");
+  return GHB_ERR_INVALID;
+}
+template ghb_status launch_row_batch<double>(int, int, const RowItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_row_batch<float>(int, int, const RowItem*, int, int64_t, size_t, cudaStream_t);
+
+template <typename T>
 ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_t s) {
-  // real lines per CTA and the resulting number of complex lines NL
-  int rows_per_cta = 1;
-  int per_row = a.nfields * a.ncomp;
-  if (mode == ROW_MATVEC || mode == ROW_TOREAL) rows_per_cta = (per_row % 2 == 1) ? 2 : 1;
-  const int nrl = rows_per_cta * per_row;
-  const int NL = (nrl + 1) / 2;
+  int rows_per_cta = 1, NL = 1;
+  row_lines(mode, a.nfields, a.ncomp, &rows_per_cta, &NL);
   if (mode == ROW_MATVEC) {
     switch (NL) {
-      case 1: return launch_row_t<T, 1, ROW_MATVEC>(a, pl, rows_per_cta, s);
-      case 3: return launch_row_t<T, 3, ROW_MATVEC>(a, pl, rows_per_cta, s);
+      case 1: return launch_row_nl<T, 1, ROW_MATVEC>(a, pl, rows_per_cta, s);
+      case 3: return launch_row_nl<T, 3, ROW_MATVEC>(a, pl, rows_per_cta, s);
       default: break;
     }
-  } else if (mode == ROW_TOREAL) {
-    if (NL == 1) return launch_row_t<T, 1, ROW_TOREAL>(a, pl, rows_per_cta, s);
-  } else {
+  } else if constexpr (sizeof(T) == 8) {   // set-up and Gram passes run in FP64 only
+    if (mode == ROW_TOREAL) {
+      if (NL == 1) return launch_row_nl<T, 1, ROW_TOREAL>(a, pl, rows_per_cta, s);
+      set_error("internal: unsupported row-pass line count");
+      return GHB_ERR_INVALID;
+    }
     switch (NL) {
-      case 1: return launch_row_t<T, 1, ROW_ENERGY>(a, pl, 1, s);
-      case 2: return launch_row_t<T, 2, ROW_ENERGY>(a, pl, 1, s);
-      case 3: return launch_row_t<T, 3, ROW_ENERGY>(a, pl, 1, s);
-      case 4: return launch_row_t<T, 4, ROW_ENERGY>(a, pl, 1, s);
-      case 5: return launch_row_t<T, 5, ROW_ENERGY>(a, pl, 1, s);
+      case 1: return launch_row_nl<T, 1, ROW_ENERGY>(a, pl, 1, s);
+      case 2: return launch_row_nl<T, 2, ROW_ENERGY>(a, pl, 1, s);
+      case 3: return launch_row_nl<T, 3, ROW_ENERGY>(a, pl, 1, s);
+      case 4: return launch_row_nl<T, 4, ROW_ENERGY>(a, pl, 1, s);
+      case 5: return launch_row_nl<T, 5, ROW_ENERGY>(a, pl, 1, s);
       default: break;
     }
   }

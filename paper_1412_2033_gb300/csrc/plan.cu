@@ -21,6 +21,62 @@ bool factor(int M, std::vector<int>& radices) {
   return m == 1 && static_cast<int>(radices.size()) <= kMaxStages;
 }
 
+struct Shape {
+  int id;
+  int r[3];
+};
+
+// Pass shapes in DIT radix order (see PassShape); longest first.
+const Shape kShapes[] = {
+    {SH_2_3_3, {2, 3, 3}}, {SH_3_3_3, {3, 3, 3}}, {SH_4_2_3, {4, 2, 3}}, {SH_2_3_5, {2, 3, 5}},
+    {SH_4_4_2, {4, 4, 2}}, {SH_2_3, {2, 3, 0}},   {SH_3_3, {3, 3, 0}},   {SH_2_5, {2, 5, 0}},
+    {SH_4_3, {4, 3, 0}},   {SH_3_5, {3, 5, 0}},   {SH_4_4, {4, 4, 0}},   {SH_4_5, {4, 5, 0}},
+    {SH_5_5, {5, 5, 0}},   {SH_4_2, {4, 2, 0}},   {SH_2, {2, 0, 0}},     {SH_3, {3, 0, 0}},
+    {SH_4, {4, 0, 0}},     {SH_5, {5, 0, 0}},
+};
+
+// Group consecutive stages into passes: at each stage take the first (longest)
+// shape that matches the next radices.
+void group_passes(FftPlan& p, int k, int maxprod) {
+  int t = 0, np = 0;
+  while (t < p.nst) {
+    int best = -1, blen = 0;
+    for (const Shape& sh : kShapes) {
+      int len = 0;
+      while (len < 3 && sh.r[len] != 0) ++len;
+      if (t + len > p.nst) continue;
+      int prod = 1;
+      for (int q = 0; q < len; ++q) prod *= sh.r[q];
+      if (prod > maxprod) continue;
+      bool ok = true;
+      for (int k = 0; k < len; ++k) ok = ok && (p.R[t + k] == sh.r[k]);
+      if (ok && len > blen) {
+        best = sh.id;
+        blen = len;
+      }
+    }
+    int prod = 1;
+    if (best < 0) {
+      best = SH_GENERIC;
+      blen = 1;
+    }
+    for (int k = 0; k < blen; ++k) prod *= p.R[t + k];
+    p.pshape[k][np] = best;
+    p.pR[k][np] = prod;
+    p.pLp[k][np] = p.Lp[t];
+    p.pdiv[k][np] = make_fastdiv(static_cast<unsigned>(p.Lp[t]));
+    ++np;
+    t += blen;
+  }
+  p.npass[k] = np;
+  for (int i = np; i < kMaxPasses; ++i) {
+    p.pshape[k][i] = SH_2;
+    p.pR[k][i] = 1;
+    p.pLp[k][i] = 1;
+    p.pdiv[k][i] = make_fastdiv(1);
+  }
+}
+
 }  // namespace
 
 bool factorizable(int M) {
@@ -56,6 +112,8 @@ ghb_status make_plan(int M, PlanHolder& out) {
     L *= radices[t];
   }
   for (int t = p.nst; t < kMaxStages; ++t) { p.R[t] = 1; p.Lp[t] = L; }
+  group_passes(p, 0, 18);   // FP64
+  group_passes(p, 1, 32);   // FP32
 
   // perm[n]: write n in mixed radix with the last stage's radix least
   // significant; the position has the digits in stage order, first stage least
@@ -82,6 +140,20 @@ ghb_status make_plan(int M, PlanHolder& out) {
     tw64[j] = make_double2(c, s);
     tw32[j] = make_float2(static_cast<float>(c), static_cast<float>(s));
   }
+  // roots of unity of small order for the register-blocked passes
+  std::vector<double2> r64(kRootTable);
+  std::vector<float2> r32(kRootTable);
+  for (int n = 1; n <= kMaxRootOrder; ++n)
+    for (int k = 0; k < n; ++k) {
+      const long double a = two_pi * static_cast<long double>(k) / static_cast<long double>(n);
+      const double c = static_cast<double>(cosl(a)), sn = -static_cast<double>(sinl(a));
+      r64[n * (n - 1) / 2 + k] = make_double2(c, sn);
+      r32[n * (n - 1) / 2 + k] = make_float2(static_cast<float>(c), static_cast<float>(sn));
+    }
+  GHB_CUDA_TRY(cudaMalloc(&out.d_roots64, sizeof(double2) * kRootTable));
+  GHB_CUDA_TRY(cudaMalloc(&out.d_roots32, sizeof(float2) * kRootTable));
+  GHB_CUDA_TRY(cudaMemcpy(out.d_roots64, r64.data(), sizeof(double2) * kRootTable, cudaMemcpyHostToDevice));
+  GHB_CUDA_TRY(cudaMemcpy(out.d_roots32, r32.data(), sizeof(float2) * kRootTable, cudaMemcpyHostToDevice));
   GHB_CUDA_TRY(cudaMalloc(&out.d_perm, sizeof(int) * M));
   GHB_CUDA_TRY(cudaMalloc(&out.d_tw64, sizeof(double2) * M));
   GHB_CUDA_TRY(cudaMalloc(&out.d_tw32, sizeof(float2) * M));
@@ -91,6 +163,8 @@ ghb_status make_plan(int M, PlanHolder& out) {
   p.perm = out.d_perm;
   p.tw64 = out.d_tw64;
   p.tw32 = out.d_tw32;
+  p.roots64 = out.d_roots64;
+  p.roots32 = out.d_roots32;
   return GHB_OK;
 }
 
@@ -98,6 +172,8 @@ void free_plan(PlanHolder& p) {
   if (p.d_perm) cudaFree(p.d_perm);
   if (p.d_tw64) cudaFree(p.d_tw64);
   if (p.d_tw32) cudaFree(p.d_tw32);
+  if (p.d_roots64) cudaFree(p.d_roots64);
+  if (p.d_roots32) cudaFree(p.d_roots32);
   p = PlanHolder{};
 }
 

@@ -28,7 +28,8 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_get_grid", "ghb_field_elems", "ghb_matvec", "ghb_solve_primal", "ghb_solve_dual",
            "ghb_gram", "ghb_bounds", "ghb_table_elems", "ghb_grid_elems", "ghb_copy_table",
            "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
-           "ghb_profile", "ghb_profile_read"]
+           "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
+           "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -51,6 +52,20 @@ class GhbSolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class GhbResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("d", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("upper", ctypes.c_double * 9), ("lower", ctypes.c_double * 9), ("info", GhbSolveInfo * 6),
+                ("seconds_queued", ctypes.c_double), ("seconds_total", ctypes.c_double)]
+
+    def as_dict(self):
+        d = self.d
+        return {"id": self.id, "d": d, "status": self.status,
+                "upper": np.array(self.upper[: d * d]).reshape(d, d),
+                "lower": np.array(self.lower[: d * d]).reshape(d, d),
+                "infos": [self.info[i].as_dict() for i in range(2 * d)],
+                "seconds_queued": self.seconds_queued, "seconds_total": self.seconds_total}
 
 
 class GhbError(RuntimeError):
@@ -98,6 +113,13 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_destroy": (None, [P]),
         "ghb_version": (ctypes.c_char_p, []),
         "ghb_profile": (i32, [P, i32]),
+        "ghb_batch_create": (i32, [ctypes.POINTER(P), ctypes.POINTER(GhbOptions), i64, i32]),
+        "ghb_batch_submit": (i32, [P, i32, ip, dbl, ctypes.POINTER(GhbPhase), i32, ctypes.POINTER(i64)]),
+        "ghb_batch_step": (i32, [P, i32, ip, ip]),
+        "ghb_batch_run": (i32, [P, i32]),
+        "ghb_batch_results": (i32, [P, ctypes.POINTER(GhbResult), i32]),
+        "ghb_batch_stats": (i32, [P, ctypes.POINTER(i64), ip, ip, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "ghb_batch_destroy": (None, [P]),
         "ghb_profile_read": (i32, [P, i32, ctypes.POINTER(i64), dp, dp, dp]),
     }
     for name, (res, args) in sig.items():
@@ -248,9 +270,10 @@ class Context:
         if tuple(x.shape) != self.field_shape or not x.is_cuda or not x.is_contiguous():
             raise ValueError(f"x must be a contiguous CUDA tensor of shape {self.field_shape}")
         y = torch.empty_like(x) if out is None else out
-        s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-        if s is None:
-            s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        handle = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        # handle 0 is the legacy default stream; the C ABI reads NULL as "the
+        # context's own stream", so name the legacy stream explicitly (0x1)
+        s = ctypes.c_void_p(handle if handle != 0 else 1)
         _check(_lib.ghb_matvec(self._h, int(kind), prec, int(bool(project)), ctypes.c_void_p(x.data_ptr()),
                                ctypes.c_void_p(y.data_ptr()), s))
         return y
@@ -304,6 +327,62 @@ class Context:
         t = torch.empty(tuple(self.M), dtype=torch.float64, device="cuda")
         _check(_lib.ghb_copy_grid_values(self._h, int(kind), ctypes.c_void_p(t.data_ptr())))
         return t
+
+
+class Batch:
+    """Many bound-pair requests solved together (C ABI ghb_batch_*): one launch
+    per kernel and CG iteration over all active solves, continuous admission."""
+
+    def __init__(self, budget_bytes=0, max_active=0, **options):
+        lib = load_library()
+        options.setdefault("precision", "mixed")
+        self.opts = Options(**options)
+        self._h = ctypes.c_void_p()
+        o = self.opts.to_c()
+        _check(lib.ghb_batch_create(ctypes.byref(self._h), ctypes.byref(o), int(budget_bytes), int(max_active)))
+        self._buf = (GhbResult * 256)()
+
+    def submit(self, m: dict) -> int:
+        Nc = (ctypes.c_int * 3)(*([int(n) for n in m["N"]] + [1] * (3 - len(m["N"]))))
+        ph, n = make_phases(m["inclusions"])
+        rid = ctypes.c_int64()
+        _check(_lib.ghb_batch_submit(self._h, int(m["d"]), Nc, float(m["a0"]), ph, n, ctypes.byref(rid)))
+        return rid.value
+
+    def step(self, iterations=8):
+        a, p = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.ghb_batch_step(self._h, int(iterations), ctypes.byref(a), ctypes.byref(p)))
+        return a.value, p.value
+
+    def run(self, iterations=8):
+        _check(_lib.ghb_batch_run(self._h, int(iterations)))
+
+    def results(self):
+        out = []
+        while True:
+            n = _lib.ghb_batch_results(self._h, self._buf, len(self._buf))
+            out.extend(self._buf[i].as_dict() for i in range(n))
+            if n < len(self._buf):
+                return out
+
+    def stats(self):
+        b, f, L = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        a, p = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.ghb_batch_stats(self._h, ctypes.byref(b), ctypes.byref(a), ctypes.byref(p), ctypes.byref(f),
+                                    ctypes.byref(L)))
+        return {"bytes_in_use": b.value, "active": a.value, "pending": p.value, "finished": f.value,
+                "launches": L.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ghb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

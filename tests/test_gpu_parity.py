@@ -68,7 +68,24 @@ def test_coefficient_table_parity(ghb, name):
         ref = tab[..., Nd - 1:]                     # n_d = 0..N_d-1
         got = ctx.table(kind).cpu().numpy()
         assert got.shape == ref.shape
-        assert rel(got, ref) < 1e-12
+        assert rel(got, ref) < 2e-14
+
+
+@pytest.mark.parametrize("N,c", [(729, (0.0, 0.0)), (301, (0.137, -0.291))])
+def test_disk_table_large_arguments(ghb, N, c):
+    """Disk coefficients at J1 arguments up to 2 pi r |k| ~ 2000: the device's
+    J1 (Miller recurrence / Hankel expansion beyond x = 8) and phase against the
+    oracle (scipy's J1).  Both evaluate J1 at the same FP64 argument, so they
+    agree to about 1e-15 of the envelope r sqrt(2/(pi x)) / |k|."""
+    m = dict(d=2, N=[N, N], a0=1.0, inclusions=[(1, (c[0], c[1], 0), (0.3090194, 0, 0), 100.0)])
+    ctx = ghb.Context.from_microstructure(m)
+    tab = OC.coeff_table(OC.material_from_dict(m), m["N"])[..., N - 1:]
+    got = ctx.table(ghb.GHB_PRIMAL).cpu().numpy()
+    k = OC.freq_grid([2 * N - 1, 2 * N - 1])[..., N - 1:, :].astype(float)
+    rho = np.maximum(np.sqrt((k ** 2).sum(-1)), 1.0)
+    env = 99.0 * 0.3090194 / rho * np.sqrt(2 / (np.pi * 2 * np.pi * 0.3090194 * rho))
+    assert np.abs(got - tab).max() / env.max() < 1e-13
+    assert (np.abs(got - tab) / env).max() < 2e-14
 
 
 @pytest.mark.parametrize("name", list(MICROS))
@@ -196,3 +213,42 @@ def test_repeatable_bitwise(ghb):
     a = ctx.bounds()
     b = ctx.bounds()
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# transform lengths exercising every pass shape of the planner: 162 = 2.3^4,
+# 486 = 2.3^5, 256 = 4^4, 216 = 4.2.3^3, 125 = 5^3, 150 = 2.3.5^2, 4374 = 2.3^7
+SIZES = [(81, None), (243, None), (127, None), (101, None), (63, None), (75, None)]
+
+
+@pytest.mark.parametrize("N,M", SIZES)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matvec_sizes(ghb, N, M, prec):
+    m = W.random_disk_instance(7 + N, N=N)
+    ctx = ghb.Context.from_microstructure(m)
+    x = W.random_field(np.random.default_rng(N), 2, [N, N])
+    op = OG.Operator(OC.material_from_dict(m), [N, N], OG.PRIMAL, M=ctx.M)
+    ref = ghb.half_from_full(op.apply(x))
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    xt = torch.from_numpy(np.ascontiguousarray(ghb.half_from_full(x))).to(dt).cuda()
+    got = ctx.matvec(xt).cpu().numpy()
+    assert rel(got, ref) < (1e-12 if prec == "f64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matvec_full_size_sampled(ghb, prec):
+    """The measured workload (d = 2 disk, N = 2187, M = 4374): the operator on a
+    random field at sampled output frequencies against the oracle's definition
+    y(l) = G(l) sum_k a^(l - k) x(k)."""
+    m = W.centred_disk(2187, fraction=0.3, value=100.0)
+    ctx = ghb.Context.from_microstructure(m)
+    assert ctx.M == [4374, 4374]
+    x = W.random_field(np.random.default_rng(2187), 2, [2187, 2187])
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    xt = torch.from_numpy(np.ascontiguousarray(ghb.half_from_full(x))).to(dt).cuda()
+    y = ctx.matvec(xt).cpu().numpy()
+    c = 1093
+    idx = np.array([[0, 0], [1, 0], [0, 1], [-1093, 1093], [1093, 0], [37, 911], [-512, 3], [700, 1093]])
+    ref = OG.matvec_sampled(x, OC.material_from_dict(m), OG.PRIMAL, idx)
+    got = np.array([y[:, l[0] + c, l[1]] for l in idx])
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() < (1e-11 if prec == "f64" else 2e-5) * scale

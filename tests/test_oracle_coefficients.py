@@ -139,3 +139,39 @@ def test_validate_rejects_bad_inputs():
     with pytest.raises(ValueError):   # overlapping through the periodic boundary
         C.validate(C.Material(2, 1.0, [C.Inclusion(C.DISK, (0.45, 0), (0.1,), 2.0),
                                        C.Inclusion(C.DISK, (-0.45, 0), (0.1,), 2.0)]))
+
+
+def test_large_argument_accuracy_against_mpmath():
+    """High frequencies (N up to 2187 reaches |n| ~ 3000): the sinc factor, the
+    disk's J1 term and the shift phase against 30-digit mpmath evaluations."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    h = 0.7071067811865476
+    for k in [1, 37, 999, 2186, 3001]:
+        ref = float(mpmath.sin(mpmath.pi * h * k) / (mpmath.pi * h * k)) * h
+        got = C.shape_coeff(C.BOX, np.array([[k, 0]]), (h, 1.0))[0].real
+        assert abs(got - ref) < 1e-16 + 1e-15 * abs(ref) + 1e-15 / k
+    r = 0.3090194
+    for k in [(3, 4), (700, 11), (2186, 2186), (1500, -900)]:
+        rho = mpmath.sqrt(k[0] ** 2 + k[1] ** 2)
+        ref = float(r * mpmath.besselj(1, 2 * mpmath.pi * r * rho) / rho)
+        got = C.shape_coeff(C.DISK, np.array([k]), (r,))[0].real
+        # FP64 rounds the argument x = 2 pi r |k| by about x eps, which moves the
+        # oscillating J1 by up to |J1'| x eps ~ envelope * x eps
+        x = 2 * math.pi * r * float(rho)
+        env = r / float(rho) * math.sqrt(2 / (math.pi * x))
+        assert abs(got - ref) < env * (x * 4e-16 + 1e-15)
+    c = (0.1234567891, -0.3141592653)
+    mat = C.Material(2, 0.0, [C.Inclusion(C.BOX, c, (1.0, 1.0), 1.0)])   # full cell: f^ = delta
+    for k in [(0, 0)]:
+        assert abs(C.coeff_at(mat, np.array([k]))[0] - 1.0) < 1e-15
+    mat = C.Material(2, 0.0, [C.Inclusion(C.DISK, c, (r,), 1.0)])
+    for k in [(2186, 1093), (-3000, 17)]:
+        t = mpmath.mpf(k[0]) * mpmath.mpf(c[0]) + mpmath.mpf(k[1]) * mpmath.mpf(c[1])
+        ph = complex(mpmath.exp(-2j * mpmath.pi * t))
+        rho = mpmath.sqrt(k[0] ** 2 + k[1] ** 2)
+        f = float(r * mpmath.besselj(1, 2 * mpmath.pi * r * rho) / rho)
+        got = C.coeff_at(mat, np.array([k]))[0]
+        x = 2 * math.pi * r * float(rho)
+        env = r / float(rho) * math.sqrt(2 / (math.pi * x))
+        assert abs(got - ph * f) < env * (x * 4e-16 + 1e-14)
