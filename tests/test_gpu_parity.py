@@ -7,7 +7,8 @@ Tolerances:
 * FP32 operator: 2e-5 relative to the largest entry (float epsilon 6e-8 times
   about 20 radix stages and the conditioning of the multiply).
 * FP64 bounds: 1e-12 relative (the stated FP64 parity target).
-* Mixed bounds: 1e-8 relative, upper >= oracle (1 - 1e-13), lower <= oracle (1 + 1e-13).
+* Mixed bounds: 1e-8 relative, upper >= oracle (1 - s), lower <= oracle (1 + s)
+  with s = max(1e-13, 1e-15 x contrast) (FP64 evaluation noise of the energies).
 """
 import zlib
 
@@ -27,6 +28,16 @@ def ghb():
     import paper_1412_2033_gb300 as g
     g.load_library()
     return g
+
+
+def one_sided_slack(m):
+    """Relative slack of the one-sided checks.  The exact energy of an
+    admissible field can never undercut the minimum, but its FP64 evaluation on
+    the double grid carries rounding of about eps log2|M| rho_A relative, rho_A
+    the contrast (the oracle's own bounds move by 1.7e-13 between two
+    admissible M at rho_A = 4e3): max(1e-13, 1e-15 rho_A)."""
+    vals = [m["a0"]] + [inc[3] for inc in m["inclusions"]]
+    return max(1e-13, 1e-15 * max(vals) / min(vals))
 
 
 def rel(a, b):
@@ -173,10 +184,11 @@ def test_bounds_mixed_parity_and_one_sided(ghb, name):
     Uo, Lo, _ = OG.bounds(oracle_material(spec), spec["N"], M=ctx.M, tol=1e-12)
     assert rel(U, Uo) < 1e-8 and rel(L, Lo) < 1e-8
     d = spec["d"]
+    sl = one_sided_slack(spec)
     for i in range(d):
-        assert U[i, i] >= Uo[i, i] * (1 - 1e-13)
-        assert L[i, i] <= Lo[i, i] * (1 + 1e-13)
-    assert np.all(np.linalg.eigvalsh(U - Uo) > -1e-13 * np.abs(Uo).max())
+        assert U[i, i] >= Uo[i, i] * (1 - sl)
+        assert L[i, i] <= Lo[i, i] * (1 + sl)
+    assert np.all(np.linalg.eigvalsh(U - Uo) > -sl * np.abs(Uo).max())
     assert any(i["matvecs_fp32"] > 0 for i in infos)
 
 
