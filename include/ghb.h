@@ -252,6 +252,30 @@ ghb_status ghb_batch_stats(const ghb_batch* b, int64_t* bytes_in_use, int* activ
 /* Release the batch (pending and running requests are dropped).  NULL is a no-op. */
 void ghb_batch_destroy(ghb_batch* b);
 
+/* ghb_gram without any device allocation (the paper has no counterpart; this
+ * is a library convenience).  For callers that cannot call cudaMalloc: code
+ * running inside another framework's memory arena that must not grow the
+ * device heap behind its back, code running with device memory reserved to
+ * the last byte, or code under a no-allocation-after-start-up policy.
+ *   d, N[d], M[d]: dimension, odd orders, double grid (M_a >= 2N_a - 1, prime
+ *     factors <= 31), as for a context;
+ *   grid_dev: the double-grid values A_M (or B_M), FP64, C-order over
+ *     m_a = 0..M_a-1 (for example from ghb_copy_grid_values);
+ *   fields_dev[0..m-1], 1 <= m <= d: FP64 half-spectrum fields (layout above);
+ *   out[m*m]: host, receives a(v_i, v_j) = (1/|M|) sum_m A_M(x_m) v_i.v_j;
+ *   stream: cudaStream_t or NULL (legacy default stream).  Synchronous.
+ * All scratch (transform tables, intermediates, partial sums) lives in one
+ * fixed 32 MiB device array that every GPU loading this library holds until
+ * the process exits; sizes needing more are rejected with GHB_ERR_INVALID
+ * and a message (d = 2 reaches N = 511 for m = 2).  The call allocates
+ * nothing (no cudaMalloc, cudaFree, or allocating library routine).  The
+ * first call on a device looks up the array's device address on that device,
+ * so make it before any stream capture.  Every call shares the one array and
+ * leaves its contents behind: calls that overlap on the GPU (other streams or
+ * host threads) race and must be serialised by the caller. */
+ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* grid_dev, int m,
+                            const void* const* fields_dev, double* out, void* stream);
+
 /* Device bytes held by the context. */
 int64_t ghb_device_bytes(const ghb_ctx* ctx);
 

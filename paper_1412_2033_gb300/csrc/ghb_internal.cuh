@@ -87,6 +87,16 @@ struct PlanHolder {
 };
 
 ghb_status make_plan(int M, PlanHolder& out);
+// Host tables of a plan (digit reversal, twiddles, small-order roots); the
+// plan's device pointers are left null for the caller to place the tables.
+struct PlanTables {
+  std::vector<int> perm;
+  std::vector<double2> tw64;
+  std::vector<float2> tw32;
+  std::vector<double2> r64;
+  std::vector<float2> r32;
+};
+ghb_status build_plan_tables(int M, FftPlan& p, PlanTables& t);
 void free_plan(PlanHolder& p);
 bool factorizable(int M);
 int auto_M(int N);

@@ -94,14 +94,13 @@ int auto_M(int N) {
   }
 }
 
-ghb_status make_plan(int M, PlanHolder& out) {
+ghb_status build_plan_tables(int M, FftPlan& p, PlanTables& t) {
   std::vector<int> radices;
   if (M < 1 || !factor(M, radices)) {
     set_error("unsupported transform length M=" + std::to_string(M) +
               " (prime factors must be <= 31)");
     return GHB_ERR_INVALID;
   }
-  FftPlan& p = out.plan;
   p = FftPlan{};
   p.M = M;
   p.nst = static_cast<int>(radices.size());
@@ -118,7 +117,8 @@ ghb_status make_plan(int M, PlanHolder& out) {
   // perm[n]: write n in mixed radix with the last stage's radix least
   // significant; the position has the digits in stage order, first stage least
   // significant.
-  std::vector<int> perm(M);
+  std::vector<int>& perm = t.perm;
+  perm.assign(M, 0);
   std::vector<int> q(p.nst > 0 ? p.nst : 1);
   for (int n = 0; n < M; ++n) {
     int rem = n;
@@ -130,8 +130,10 @@ ghb_status make_plan(int M, PlanHolder& out) {
     for (int t = 0; t < p.nst; ++t) pos += q[t] * p.Lp[t];
     perm[n] = pos;
   }
-  std::vector<double2> tw64(M);
-  std::vector<float2> tw32(M);
+  std::vector<double2>& tw64 = t.tw64;
+  std::vector<float2>& tw32 = t.tw32;
+  tw64.resize(M);
+  tw32.resize(M);
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int j = 0; j < M; ++j) {
     long double ang = two_pi * static_cast<long double>(j) / static_cast<long double>(M);
@@ -141,8 +143,10 @@ ghb_status make_plan(int M, PlanHolder& out) {
     tw32[j] = make_float2(static_cast<float>(c), static_cast<float>(s));
   }
   // roots of unity of small order for the register-blocked passes
-  std::vector<double2> r64(kRootTable);
-  std::vector<float2> r32(kRootTable);
+  std::vector<double2>& r64 = t.r64;
+  std::vector<float2>& r32 = t.r32;
+  r64.resize(kRootTable);
+  r32.resize(kRootTable);
   for (int n = 1; n <= kMaxRootOrder; ++n)
     for (int k = 0; k < n; ++k) {
       const long double a = two_pi * static_cast<long double>(k) / static_cast<long double>(n);
@@ -150,6 +154,19 @@ ghb_status make_plan(int M, PlanHolder& out) {
       r64[n * (n - 1) / 2 + k] = make_double2(c, sn);
       r32[n * (n - 1) / 2 + k] = make_float2(static_cast<float>(c), static_cast<float>(sn));
     }
+  return GHB_OK;
+}
+
+ghb_status make_plan(int M, PlanHolder& out) {
+  PlanTables t;
+  ghb_status st = build_plan_tables(M, out.plan, t);
+  if (st != GHB_OK) return st;
+  FftPlan& p = out.plan;
+  const std::vector<int>& perm = t.perm;
+  const std::vector<double2>& tw64 = t.tw64;
+  const std::vector<float2>& tw32 = t.tw32;
+  const std::vector<double2>& r64 = t.r64;
+  const std::vector<float2>& r32 = t.r32;
   GHB_CUDA_TRY(cudaMalloc(&out.d_roots64, sizeof(double2) * kRootTable));
   GHB_CUDA_TRY(cudaMalloc(&out.d_roots32, sizeof(float2) * kRootTable));
   GHB_CUDA_TRY(cudaMemcpy(out.d_roots64, r64.data(), sizeof(double2) * kRootTable, cudaMemcpyHostToDevice));

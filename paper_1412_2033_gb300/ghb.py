@@ -29,7 +29,7 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_gram", "ghb_bounds", "ghb_table_elems", "ghb_grid_elems", "ghb_copy_table",
            "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
            "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
-           "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy"]
+           "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -120,6 +120,7 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_batch_results": (i32, [P, ctypes.POINTER(GhbResult), i32]),
         "ghb_batch_stats": (i32, [P, ctypes.POINTER(i64), ip, ip, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "ghb_batch_destroy": (None, [P]),
+        "ghb_gram_noalloc": (i32, [i32, ip, ip, P, i32, ctypes.POINTER(P), dp, P]),
         "ghb_profile_read": (i32, [P, i32, ctypes.POINTER(i64), dp, dp, dp]),
     }
     for name, (res, args) in sig.items():
@@ -327,6 +328,21 @@ class Context:
         t = torch.empty(tuple(self.M), dtype=torch.float64, device="cuda")
         _check(_lib.ghb_copy_grid_values(self._h, int(kind), ctypes.c_void_p(t.data_ptr())))
         return t
+
+
+def gram_noalloc(d, N, M, grid, fields, stream=None):
+    """ghb_gram_noalloc: the Gram matrix of FP64 half-spectrum fields without any
+    device allocation (scratch in a fixed 32 MiB device array; for callers that
+    cannot allocate).  grid: FP64 CUDA tensor of the double-grid values."""
+    lib = load_library()
+    Nc = (ctypes.c_int * 3)(*([int(n) for n in N] + [1] * (3 - len(N))))
+    Mc = (ctypes.c_int * 3)(*([int(n) for n in M] + [1] * (3 - len(M))))
+    ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in fields])
+    out = (ctypes.c_double * 9)()
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(lib.ghb_gram_noalloc(int(d), Nc, Mc, ctypes.c_void_p(grid.data_ptr()), len(fields), ptrs, out, s))
+    m = len(fields)
+    return np.array(out[: m * m]).reshape(m, m)
 
 
 class Batch:
