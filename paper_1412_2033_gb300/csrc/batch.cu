@@ -425,10 +425,11 @@ ghb_status prep_row(ghb_batch* b, int mode, std::vector<RowItem>& items, const s
                     int ncomp, std::vector<Launch>& out) {
   if (items.empty()) return GHB_OK;
   using C = typename CT<T>::type;
-  int rpc = 1, NL = 1;
-  row_lines(mode, nfields, ncomp, &rpc, &NL);
   int Mmax = 1;
   for (int M : Ms) Mmax = std::max(Mmax, M);
+  int rpc = 1, NL = 1;
+  set_row_plan_length(Mmax);
+  row_lines(mode, nfields, ncomp, &rpc, &NL);
   int64_t blocks = 0;
   for (auto& it : items) {
     it.rows_per_cta = rpc;

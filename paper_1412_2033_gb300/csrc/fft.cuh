@@ -31,7 +31,7 @@
 // round trip and one barrier per pass instead of per stage.  Twiddles: the
 // stage-s factor w_{L_s}^{(p + j' L_{t-1}) q} = (w_{L_s}^p w_{sigma rho}^{j'})^q is a
 // table load per pass and sub-stage (w_{L_s}^p) times a root of unity of small
-// order held in constant memory, raised to the power q by multiplication.
+// order that the compiler evaluates, raised to the power q by multiplication.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,7 +42,6 @@ namespace ghb {
 constexpr int kMaxStages = 24;
 constexpr int kMaxPasses = 24;
 constexpr int kMaxGenericRadix = 31;
-constexpr int kMaxRootOrder = 32;     // roots w_n^k tabulated for n <= 32
 
 // Division by an invariant 32-bit integer with a multiply-high (Granlund and
 // Montgomery, "Division by invariant integers using multiplication", 1994,
@@ -98,10 +97,10 @@ struct FftPlan {
   int pLp[2][kMaxPasses];       // L_{t-1} of its first stage
   FastDiv pdiv[2][kMaxPasses];  // division by pLp
   const int* perm;           // perm[n]: digit-reversed position of index n
+  const int* perm_ct;        // the same for the stage order of fft_ct.cuh (null if M has no
+                             // size-specialised kernels)
   const double2* tw64;       // tw64[j] = exp(-2 pi i j / M)
   const float2* tw32;        // the same rounded to float
-  const double2* roots64;    // roots of unity of order <= 32 (see croot)
-  const float2* roots32;
 };
 
 template <typename T> struct CT;
@@ -138,9 +137,6 @@ __device__ __forceinline__ C rot(C a) {
 template <typename C> __device__ __forceinline__ const C* twtab(const FftPlan& p);
 template <> __device__ __forceinline__ const double2* twtab<double2>(const FftPlan& p) { return p.tw64; }
 template <> __device__ __forceinline__ const float2* twtab<float2>(const FftPlan& p) { return p.tw32; }
-template <typename C> __device__ __forceinline__ const C* roottab(const FftPlan& p);
-template <> __device__ __forceinline__ const double2* roottab<double2>(const FftPlan& p) { return p.roots64; }
-template <> __device__ __forceinline__ const float2* roottab<float2>(const FftPlan& p) { return p.roots32; }
 
 // Padded shared-memory index: one spare slot every 128 bytes of data.
 template <typename C>
@@ -148,21 +144,61 @@ __device__ __forceinline__ int pidx(int i) {
   return sizeof(C) == 8 ? i + (i >> 4) : i + (i >> 3);
 }
 template <typename C>
-__host__ __device__ inline size_t padded_elems(size_t n) {
+__host__ __device__ constexpr size_t padded_elems(size_t n) {
   return sizeof(C) == 8 ? n + (n >> 4) + 1 : n + (n >> 3) + 1;
 }
 
 // ---------------------------------------------------------------------------
-// roots of unity of small order (a per-plan device table, read with uniform
-// addresses so a warp's load is one broadcast transaction):
-//   roots[n (n - 1) / 2 + k] = exp(-2 pi i k / n),  1 <= n <= 32, k < n
+// roots of unity of small order, evaluated by the compiler:
+//   exp(-2 pi i k / n) = (root_cos(k, n), -root_sin(k, n))
+// k / n is reduced to [0, 1/8] by the symmetries of the circle (exact integer
+// comparisons), and cos / sin of the remaining angle x <= pi/4 are the sums of
+// their Taylor series, whose terms fall below 1e-20 after 12 steps.
 // ---------------------------------------------------------------------------
-constexpr int kRootTable = kMaxRootOrder * (kMaxRootOrder + 1) / 2;
+constexpr double kTwoPi = 6.28318530717958647692528676655900577;
 
-template <typename C>
-__device__ __forceinline__ C croot(const C* __restrict__ roots, int n, int k) {
-  return __ldg(&roots[n * (n - 1) / 2 + k]);
+__host__ __device__ constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 12; ++i) {
+    t *= -x * x / static_cast<double>((2 * i) * (2 * i + 1));
+    s += t;
+  }
+  return s;
 }
+__host__ __device__ constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 12; ++i) {
+    t *= -x * x / static_cast<double>((2 * i - 1) * (2 * i));
+    s += t;
+  }
+  return s;
+}
+// cos(2 pi k / n) (want_sin = false) or sin(2 pi k / n) (want_sin = true)
+__host__ __device__ constexpr double root_trig(int k, int n, bool want_sin) {
+  k %= n;
+  if (k < 0) k += n;
+  double sign = 1.0;
+  if (2 * k > n) {                 // theta > pi: sin(2 pi - theta) = -sin theta
+    k = n - k;
+    if (want_sin) sign = -sign;
+  }
+  // now theta = 2 pi k / n in [0, pi]; write theta = pi - phi if theta > pi/2
+  if (4 * k > n) {                 // cos(pi - phi) = -cos phi, sin(pi - phi) = sin phi
+    k = n - 2 * k;                 // phi = 2 pi k / (2 n)
+    n = 2 * n;
+    if (!want_sin) sign = -sign;
+  }
+  // theta = 2 pi k / n in [0, pi/2]; use the complement above pi/4
+  if (8 * k > n) {
+    const int kc = n - 4 * k;      // pi/2 - theta = 2 pi kc / (4 n)
+    const double x = kTwoPi * static_cast<double>(kc) / static_cast<double>(4 * n);
+    return sign * (want_sin ? taylor_cos(x) : taylor_sin(x));
+  }
+  const double x = kTwoPi * static_cast<double>(k) / static_cast<double>(n);
+  return sign * (want_sin ? taylor_sin(x) : taylor_cos(x));
+}
+__host__ __device__ constexpr double root_cos(int k, int n) { return root_trig(k, n, false); }
+__host__ __device__ constexpr double root_sin(int k, int n) { return root_trig(k, n, true); }
 
 // ---------------------------------------------------------------------------
 // small DFTs X_k = sum_n x_n exp(SIGN 2 pi i n k / R), in registers
@@ -231,42 +267,54 @@ __device__ __forceinline__ void dft_small(C* v) {
 //   pass, RG: radix product of the whole pass; v holds the pass's RG entries
 //   (entry j at position b L_g + p + j Lp).  ts = M / (Lp SIG RHO).
 // ---------------------------------------------------------------------------
-template <int SIGN, bool DIT, int RHO, int SIG, int RG, typename C>
-__device__ __forceinline__ void substage(C* v, int p, int ts, const C* __restrict__ tw,
-                                         const C* __restrict__ roots) {
-  const C wb = __ldg(&tw[p * ts]);   // w_{L_s}^p, L_s = Lp SIG RHO
-#pragma unroll
-  for (int jp = 0; jp < SIG; ++jp) {
-    C t1 = (jp == 0) ? wb : cmul(wb, croot<C>(roots, SIG * RHO, jp));
-    C tq[RHO];
-    tq[0] = mk(decltype(wb.x)(1), decltype(wb.x)(0));
-    if constexpr (RHO > 1) tq[1] = t1;
-#pragma unroll
-    for (int q = 2; q < RHO; ++q) tq[q] = cmul(tq[q - 1], t1);
-#pragma unroll
-    for (int jb = 0; jb < RG / (SIG * RHO); ++jb) {
-      C e[RHO];
-#pragma unroll
-      for (int q = 0; q < RHO; ++q) e[q] = v[jb * SIG * RHO + jp + q * SIG];
-      if (DIT) {
-#pragma unroll
-        for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
-      }
-      dft_small<SIGN, RHO>(e);
-      if (!DIT) {
-#pragma unroll
-        for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
-      }
-#pragma unroll
-      for (int q = 0; q < RHO; ++q) v[jb * SIG * RHO + jp + q * SIG] = e[q];
-    }
+template <int SIGN, bool DIT, int RHO, int SIG, int RG, int JP, typename C>
+__device__ __forceinline__ void substage_jp(C* v, C wb) {
+  using R = decltype(wb.x);
+  C t1 = wb;
+  if constexpr (JP > 0) {
+    constexpr double cr = root_cos(JP, SIG * RHO), sr = -root_sin(JP, SIG * RHO);
+    t1 = cmul(wb, mk(R(cr), R(sr)));
   }
+  C tq[RHO];
+  tq[0] = mk(R(1), R(0));
+  if constexpr (RHO > 1) tq[1] = t1;
+#pragma unroll
+  for (int q = 2; q < RHO; ++q) tq[q] = cmul(tq[q - 1], t1);
+#pragma unroll
+  for (int jb = 0; jb < RG / (SIG * RHO); ++jb) {
+    C e[RHO];
+#pragma unroll
+    for (int q = 0; q < RHO; ++q) e[q] = v[jb * SIG * RHO + JP + q * SIG];
+    if (DIT) {
+#pragma unroll
+      for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
+    }
+    dft_small<SIGN, RHO>(e);
+    if (!DIT) {
+#pragma unroll
+      for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RHO; ++q) v[jb * SIG * RHO + JP + q * SIG] = e[q];
+  }
+  if constexpr (JP + 1 < SIG) substage_jp<SIGN, DIT, RHO, SIG, RG, JP + 1>(v, wb);
+}
+
+// One sub-stage of a register-blocked pass.  RHO: radix of the stage, SIG:
+// product of the radices before it inside the pass, RG: radix product of the
+// whole pass; v holds the pass's RG entries (entry j at position
+// b L_g + p + j Lp).  ts = M / (Lp SIG RHO).  The sub-stage's twiddle for
+// entry offset jp < SIG is w_{L_s}^p times the compile-time root w_{SIG RHO}^jp.
+template <int SIGN, bool DIT, int RHO, int SIG, int RG, typename C>
+__device__ __forceinline__ void substage(C* v, int p, int ts, const C* __restrict__ tw) {
+  const C wb = __ldg(&tw[p * ts]);   // w_{L_s}^p, L_s = Lp SIG RHO
+  substage_jp<SIGN, DIT, RHO, SIG, RG, 0>(v, wb);
 }
 
 // A pass of up to three stages (radices RA, RB, RC in DIT order; 1 = absent).
 template <int SIGN, bool DIT, int NL, int RA, int RB, int RC, typename C>
 __device__ __forceinline__ void run_pass(C* buf, int M, int Lp, const FastDiv& dv,
-                                         const C* __restrict__ tw, const C* __restrict__ roots) {
+                                         const C* __restrict__ tw) {
   constexpr int RG = RA * RB * RC;
   const int units = M / RG;
   const int tsA = M / (Lp * RA);
@@ -283,13 +331,13 @@ __device__ __forceinline__ void run_pass(C* buf, int M, int Lp, const FastDiv& d
 #pragma unroll
     for (int j = 0; j < RG; ++j) v[j] = buf[pidx<C>(base + j * step)];
     if (DIT) {
-      substage<SIGN, DIT, RA, 1, RG>(v, p, tsA, tw, roots);
-      if constexpr (RB > 1) substage<SIGN, DIT, RB, RA, RG>(v, p, tsB, tw, roots);
-      if constexpr (RC > 1) substage<SIGN, DIT, RC, RA * RB, RG>(v, p, tsC, tw, roots);
+      substage<SIGN, DIT, RA, 1, RG>(v, p, tsA, tw);
+      if constexpr (RB > 1) substage<SIGN, DIT, RB, RA, RG>(v, p, tsB, tw);
+      if constexpr (RC > 1) substage<SIGN, DIT, RC, RA * RB, RG>(v, p, tsC, tw);
     } else {
-      if constexpr (RC > 1) substage<SIGN, DIT, RC, RA * RB, RG>(v, p, tsC, tw, roots);
-      if constexpr (RB > 1) substage<SIGN, DIT, RB, RA, RG>(v, p, tsB, tw, roots);
-      substage<SIGN, DIT, RA, 1, RG>(v, p, tsA, tw, roots);
+      if constexpr (RC > 1) substage<SIGN, DIT, RC, RA * RB, RG>(v, p, tsC, tw);
+      if constexpr (RB > 1) substage<SIGN, DIT, RB, RA, RG>(v, p, tsB, tw);
+      substage<SIGN, DIT, RA, 1, RG>(v, p, tsA, tw);
     }
 #pragma unroll
     for (int j = 0; j < RG; ++j) buf[pidx<C>(base + j * step)] = v[j];
@@ -363,34 +411,34 @@ __device__ __forceinline__ int load_passes(PassSmem& s, const FftPlan& p) {
 // and leaving them out keeps the FP64 kernels' register allocation small).
 template <int SIGN, bool DIT, int NL, int RA, int RB, int RC, typename C>
 __device__ __forceinline__ void run_pass_p(C* buf, int M, int Lp, const FastDiv& dv,
-                                           const C* __restrict__ tw, const C* __restrict__ roots) {
-  if constexpr (sizeof(C) == 8 || RA * RB * RC <= 18) run_pass<SIGN, DIT, NL, RA, RB, RC>(buf, M, Lp, dv, tw, roots);
+                                           const C* __restrict__ tw) {
+  if constexpr (sizeof(C) == 8 || RA * RB * RC <= 18) run_pass<SIGN, DIT, NL, RA, RB, RC>(buf, M, Lp, dv, tw);
 }
 
 template <int SIGN, bool DIT, int NL, typename C>
 __device__ __forceinline__ void dispatch_pass(C* buf, int M, const PassSmem& ps, int i,
-                                              const C* __restrict__ tw, const C* __restrict__ roots) {
+                                              const C* __restrict__ tw) {
   const int Lp = ps.Lp[i];
   const FastDiv dv = ps.dv[i];
   switch (ps.shape[i]) {
-    case SH_2: run_pass_p<SIGN, DIT, NL, 2, 1, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_3: run_pass_p<SIGN, DIT, NL, 3, 1, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4: run_pass_p<SIGN, DIT, NL, 4, 1, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_5: run_pass_p<SIGN, DIT, NL, 5, 1, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_2_3: run_pass_p<SIGN, DIT, NL, 2, 3, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_3_3: run_pass_p<SIGN, DIT, NL, 3, 3, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_2_5: run_pass_p<SIGN, DIT, NL, 2, 5, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4_3: run_pass_p<SIGN, DIT, NL, 4, 3, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_3_5: run_pass_p<SIGN, DIT, NL, 3, 5, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4_4: run_pass_p<SIGN, DIT, NL, 4, 4, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4_5: run_pass_p<SIGN, DIT, NL, 4, 5, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_5_5: run_pass_p<SIGN, DIT, NL, 5, 5, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4_2: run_pass_p<SIGN, DIT, NL, 4, 2, 1>(buf, M, Lp, dv, tw, roots); break;
-    case SH_2_3_3: run_pass_p<SIGN, DIT, NL, 2, 3, 3>(buf, M, Lp, dv, tw, roots); break;
-    case SH_3_3_3: run_pass_p<SIGN, DIT, NL, 3, 3, 3>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4_2_3: run_pass_p<SIGN, DIT, NL, 4, 2, 3>(buf, M, Lp, dv, tw, roots); break;
-    case SH_2_3_5: run_pass_p<SIGN, DIT, NL, 2, 3, 5>(buf, M, Lp, dv, tw, roots); break;
-    case SH_4_4_2: run_pass_p<SIGN, DIT, NL, 4, 4, 2>(buf, M, Lp, dv, tw, roots); break;
+    case SH_2: run_pass_p<SIGN, DIT, NL, 2, 1, 1>(buf, M, Lp, dv, tw); break;
+    case SH_3: run_pass_p<SIGN, DIT, NL, 3, 1, 1>(buf, M, Lp, dv, tw); break;
+    case SH_4: run_pass_p<SIGN, DIT, NL, 4, 1, 1>(buf, M, Lp, dv, tw); break;
+    case SH_5: run_pass_p<SIGN, DIT, NL, 5, 1, 1>(buf, M, Lp, dv, tw); break;
+    case SH_2_3: run_pass_p<SIGN, DIT, NL, 2, 3, 1>(buf, M, Lp, dv, tw); break;
+    case SH_3_3: run_pass_p<SIGN, DIT, NL, 3, 3, 1>(buf, M, Lp, dv, tw); break;
+    case SH_2_5: run_pass_p<SIGN, DIT, NL, 2, 5, 1>(buf, M, Lp, dv, tw); break;
+    case SH_4_3: run_pass_p<SIGN, DIT, NL, 4, 3, 1>(buf, M, Lp, dv, tw); break;
+    case SH_3_5: run_pass_p<SIGN, DIT, NL, 3, 5, 1>(buf, M, Lp, dv, tw); break;
+    case SH_4_4: run_pass_p<SIGN, DIT, NL, 4, 4, 1>(buf, M, Lp, dv, tw); break;
+    case SH_4_5: run_pass_p<SIGN, DIT, NL, 4, 5, 1>(buf, M, Lp, dv, tw); break;
+    case SH_5_5: run_pass_p<SIGN, DIT, NL, 5, 5, 1>(buf, M, Lp, dv, tw); break;
+    case SH_4_2: run_pass_p<SIGN, DIT, NL, 4, 2, 1>(buf, M, Lp, dv, tw); break;
+    case SH_2_3_3: run_pass_p<SIGN, DIT, NL, 2, 3, 3>(buf, M, Lp, dv, tw); break;
+    case SH_3_3_3: run_pass_p<SIGN, DIT, NL, 3, 3, 3>(buf, M, Lp, dv, tw); break;
+    case SH_4_2_3: run_pass_p<SIGN, DIT, NL, 4, 2, 3>(buf, M, Lp, dv, tw); break;
+    case SH_2_3_5: run_pass_p<SIGN, DIT, NL, 2, 3, 5>(buf, M, Lp, dv, tw); break;
+    case SH_4_4_2: run_pass_p<SIGN, DIT, NL, 4, 4, 2>(buf, M, Lp, dv, tw); break;
     default: run_generic<SIGN, DIT, NL>(buf, M, ps.R[i], Lp, dv, tw); break;
   }
 }
@@ -398,18 +446,18 @@ __device__ __forceinline__ void dispatch_pass(C* buf, int M, const PassSmem& ps,
 // Decimation in time: digit-reversed input -> natural output.  The caller
 // must __syncthreads() after filling buf; returns after a final barrier.
 template <int SIGN, int NL, typename C>
-__device__ void fft_dit(C* buf, const PassSmem& ps, int npass, int M, const C* tw, const C* roots) {
+__device__ void fft_dit(C* buf, const PassSmem& ps, int npass, int M, const C* tw) {
   for (int i = 0; i < npass; ++i) {
-    dispatch_pass<SIGN, true, NL>(buf, M, ps, i, tw, roots);
+    dispatch_pass<SIGN, true, NL>(buf, M, ps, i, tw);
     __syncthreads();
   }
 }
 
 // Decimation in frequency: natural input -> digit-reversed output.
 template <int SIGN, int NL, typename C>
-__device__ void fft_dif(C* buf, const PassSmem& ps, int npass, int M, const C* tw, const C* roots) {
+__device__ void fft_dif(C* buf, const PassSmem& ps, int npass, int M, const C* tw) {
   for (int i = npass - 1; i >= 0; --i) {
-    dispatch_pass<SIGN, false, NL>(buf, M, ps, i, tw, roots);
+    dispatch_pass<SIGN, false, NL>(buf, M, ps, i, tw);
     __syncthreads();
   }
 }

@@ -80,21 +80,18 @@ struct Geometry {
 struct PlanHolder {
   FftPlan plan{};
   int* d_perm = nullptr;
+  int* d_perm_ct = nullptr;
   double2* d_tw64 = nullptr;
   float2* d_tw32 = nullptr;
-  double2* d_roots64 = nullptr;
-  float2* d_roots32 = nullptr;
 };
 
 ghb_status make_plan(int M, PlanHolder& out);
-// Host tables of a plan (digit reversal, twiddles, small-order roots); the
+// Host tables of a plan (digit reversal, twiddles); the
 // plan's device pointers are left null for the caller to place the tables.
 struct PlanTables {
   std::vector<int> perm;
   std::vector<double2> tw64;
   std::vector<float2> tw32;
-  std::vector<double2> r64;
-  std::vector<float2> r32;
 };
 ghb_status build_plan_tables(int M, FftPlan& p, PlanTables& t);
 void free_plan(PlanHolder& p);
@@ -174,6 +171,10 @@ ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64
                             cudaStream_t s);
 // rows per CTA and interleaved complex lines of a row pass
 void row_lines(int mode, int nfields, int ncomp, int* rows_per_cta, int* NL);
+// 1 or 2 rows per CTA in the d = 2 operator's last-axis pass (0 = by size)
+void set_matvec_rows(int r);
+// transform length the next row_lines call plans for (batched launches)
+void set_row_plan_length(int M);
 
 // Field-level kernels (half-spectrum fields of one context).
 struct FieldGeom {
@@ -236,7 +237,24 @@ ghb_status launch_add_constant(double2* v, const double2* e, const FieldGeom& fg
 // ---------------------------------------------------------------------------
 // shared-memory sizing
 // ---------------------------------------------------------------------------
-int col_tile_width(int M, int elem_bytes);
-size_t col_smem_bytes(int M, int TW, int elem_bytes);
+// Shared memory of a column tile and the widest tile within ~160 KB (measured:
+// 4 FP32 lines of M = 4374 per CTA beat 2 lines at two CTAs per SM by 6-14 %).
+__host__ __device__ constexpr size_t col_smem_bytes(int M, int TW, int elem_bytes) {
+  return elem_bytes == 8 ? padded_elems<float2>(static_cast<size_t>(M) * TW) * 8
+                         : padded_elems<double2>(static_cast<size_t>(M) * TW) * 16;
+}
+__host__ __device__ constexpr int col_tile_width(int M, int elem_bytes) {
+  const size_t budget = 160 * 1024;
+  for (int tw : {16, 8, 4, 2}) {
+    if (col_smem_bytes(M, tw, elem_bytes) <= budget) return tw;
+  }
+  return 1;
+}
+
+// Transform lengths with size-specialised FP32 operator kernels (fft_ct.cuh):
+// the double grids 2 * 3^k of the 2-D operator at N = 81, 243, 729, 2187.
+__host__ __device__ constexpr bool ct_size(int M) { return M == 162 || M == 486 || M == 1458 || M == 4374; }
+ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
+ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
 
 }  // namespace ghb

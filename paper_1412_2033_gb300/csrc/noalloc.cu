@@ -122,13 +122,12 @@ ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* gri
 
   // scratch layout: tables, intermediates, partial sums, ticket, Gram
   size_t need = 0;
-  size_t off_tab[3][5] = {{0}};
+  size_t off_tab[3][3] = {{0}};
   for (int a = 0; a < d; ++a) {
     if (plan_of[a] != a) continue;
-    const size_t sz[5] = {sizeof(int) * tab[a].perm.size(), sizeof(double2) * tab[a].tw64.size(),
-                          sizeof(float2) * tab[a].tw32.size(), sizeof(double2) * tab[a].r64.size(),
-                          sizeof(float2) * tab[a].r32.size()};
-    for (int k = 0; k < 5; ++k) {
+    const size_t sz[3] = {sizeof(int) * tab[a].perm.size(), sizeof(double2) * tab[a].tw64.size(),
+                          sizeof(float2) * tab[a].tw32.size()};
+    for (int k = 0; k < 3; ++k) {
       off_tab[a][k] = need;
       need += al256(sz[k]);
     }
@@ -170,15 +169,9 @@ ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* gri
                                  cudaMemcpyHostToDevice, s));
     GHB_CUDA_TRY(cudaMemcpyAsync(base + off_tab[a][2], tab[a].tw32.data(), sizeof(float2) * tab[a].tw32.size(),
                                  cudaMemcpyHostToDevice, s));
-    GHB_CUDA_TRY(cudaMemcpyAsync(base + off_tab[a][3], tab[a].r64.data(), sizeof(double2) * tab[a].r64.size(),
-                                 cudaMemcpyHostToDevice, s));
-    GHB_CUDA_TRY(cudaMemcpyAsync(base + off_tab[a][4], tab[a].r32.data(), sizeof(float2) * tab[a].r32.size(),
-                                 cudaMemcpyHostToDevice, s));
     pl[a].perm = reinterpret_cast<const int*>(base + off_tab[a][0]);
     pl[a].tw64 = reinterpret_cast<const double2*>(base + off_tab[a][1]);
     pl[a].tw32 = reinterpret_cast<const float2*>(base + off_tab[a][2]);
-    pl[a].roots64 = reinterpret_cast<const double2*>(base + off_tab[a][3]);
-    pl[a].roots32 = reinterpret_cast<const float2*>(base + off_tab[a][4]);
   }
   // the Gram pass's completion counter must start at zero on every call
   GHB_CUDA_TRY(cudaMemsetAsync(base + off_ticket, 0, 256, s));

@@ -19,22 +19,8 @@
 
 namespace ghb {
 
-size_t col_smem_bytes(int M, int TW, int elem_bytes) {
-  return elem_bytes == 8 ? padded_elems<float2>(static_cast<size_t>(M) * TW) * 8
-                         : padded_elems<double2>(static_cast<size_t>(M) * TW) * 16;
-}
-
-// Widest tile that keeps two CTAs per SM (<= ~110 KB of shared memory).
-int col_tile_width(int M, int elem_bytes) {
-  const size_t budget = 110 * 1024;
-  for (int tw : {16, 8, 4, 2}) {
-    if (col_smem_bytes(M, tw, elem_bytes) <= budget) return tw;
-  }
-  return 1;
-}
-
 // Launchers defined by instantiation in the col_*.cu / row_*.cu units.
-template <typename T, int TW>
+template <typename T, int TW, int MCT = 0>
 ghb_status launch_col_tw(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
 template <typename T, int NL, int MODE>
 ghb_status launch_row_nl(const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
@@ -44,9 +30,39 @@ ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, 
 template <typename T, int NL, int MODE>
 ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size_t smem, cudaStream_t s);
 
+template <int M>
+ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
+template <int M>
+ghb_status launch_row_ct_m(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
+
+ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
+  switch (pl.M) {
+    case 162: return launch_col_ct_m<162>(sign, mode, a, pl, s);
+    case 486: return launch_col_ct_m<486>(sign, mode, a, pl, s);
+    case 1458: return launch_col_ct_m<1458>(sign, mode, a, pl, s);
+    case 4374: return launch_col_ct_m<4374>(sign, mode, a, pl, s);
+    default: break;
+  }
+  set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
+  return GHB_ERR_INVALID;
+}
+
+ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s) {
+  switch (pl.M) {
+    case 162: return launch_row_ct_m<162>(NL, a, pl, rows_per_cta, s);
+    case 486: return launch_row_ct_m<486>(NL, a, pl, rows_per_cta, s);
+    case 1458: return launch_row_ct_m<1458>(NL, a, pl, rows_per_cta, s);
+    case 4374: return launch_row_ct_m<4374>(NL, a, pl, rows_per_cta, s);
+    default: break;
+  }
+  set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
+  return GHB_ERR_INVALID;
+}
+
 template <typename T>
 ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   using C = typename CT<T>::type;
+  if (sizeof(T) == 4 && pl.perm_ct != nullptr && ct_size(pl.M)) return launch_col_ct(sign, mode, a, pl, s);
   const int TW = col_tile_width(pl.M, sizeof(C));
   if (col_smem_bytes(pl.M, TW, sizeof(C)) > 220 * 1024) {
     set_error("transform length too large for one CTA: M=" + std::to_string(pl.M));
@@ -67,10 +83,19 @@ ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, c
 template ghb_status launch_col<double>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 template ghb_status launch_col<float>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 
+// Rows a CTA transforms together in the operator's last-axis pass (d = 2:
+// 1 or 2; odd line counts always pair two rows).  0 = by size: two rows for
+// M <= 2048 (measured 29 % faster at M = 510), one row above.
+static int g_matvec_rows = 0;
+void set_matvec_rows(int r) { g_matvec_rows = (r == 1 || r == 2) ? r : 0; }
+static int g_row_M = 0;   // transform length of the pass being planned
+void set_row_plan_length(int M) { g_row_M = M; }
+
 void row_lines(int mode, int nfields, int ncomp, int* rows_per_cta, int* NL) {
   const int per_row = nfields * ncomp;
   int r = 1;
   if (mode == ROW_MATVEC || mode == ROW_TOREAL) r = (per_row % 2 == 1) ? 2 : 1;
+  if (mode == ROW_MATVEC && per_row == 2) r = g_matvec_rows ? g_matvec_rows : (g_row_M <= 2048 ? 2 : 1);
   *rows_per_cta = r;
   *NL = (r * per_row + 1) / 2;
 }
@@ -97,6 +122,7 @@ ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64
                             cudaStream_t s) {
   if (mode == ROW_MATVEC) {
     if (NL == 1) return launch_row_batch_nl<T, 1, ROW_MATVEC>(items, n, blocks, smem, s);
+    if (NL == 2) return launch_row_batch_nl<T, 2, ROW_MATVEC>(items, n, blocks, smem, s);
     if (NL == 3) return launch_row_batch_nl<T, 3, ROW_MATVEC>(items, n, blocks, smem, s);
   } else if constexpr (sizeof(T) == 8) {
     if (mode == ROW_TOREAL && NL == 1) return launch_row_batch_nl<T, 1, ROW_TOREAL>(items, n, blocks, smem, s);
@@ -120,10 +146,13 @@ template ghb_status launch_row_batch<float>(int, int, const RowItem*, int, int64
 template <typename T>
 ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_t s) {
   int rows_per_cta = 1, NL = 1;
+  g_row_M = pl.M;
   row_lines(mode, a.nfields, a.ncomp, &rows_per_cta, &NL);
   if (mode == ROW_MATVEC) {
+    if (sizeof(T) == 4 && pl.perm_ct != nullptr && ct_size(pl.M)) return launch_row_ct(NL, a, pl, rows_per_cta, s);
     switch (NL) {
       case 1: return launch_row_nl<T, 1, ROW_MATVEC>(a, pl, rows_per_cta, s);
+      case 2: return launch_row_nl<T, 2, ROW_MATVEC>(a, pl, rows_per_cta, s);
       case 3: return launch_row_nl<T, 3, ROW_MATVEC>(a, pl, rows_per_cta, s);
       default: break;
     }

@@ -20,15 +20,49 @@
 
 #include <cmath>
 
+#include "fft_ct.cuh"
 #include "ghb_internal.cuh"
 #include "reduce.cuh"
 
 namespace ghb {
 
 // ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async): every thread issues its
+// copies back to back and waits once, so a CTA's loads are all in flight
+// together instead of one dependent load per loop iteration.
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst_smem, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory index of entry i: padded for the runtime-plan transform,
+// plain for the size-specialised one (MCT = its compile-time length).
+template <int MCT, typename C>
+__device__ __forceinline__ int bix(int i) {
+  if constexpr (MCT != 0) return i;
+  else return pidx<C>(i);
+}
+
+// Threads of a column-pass CTA.
+template <typename T, int TW, int MCT>
+__host__ __device__ constexpr int col_threads() {
+  if constexpr (MCT != 0) return MCT * TW >= 2048 ? 512 : 256;
+  else return sizeof(T) == 8 ? 256 : 512;
+}
+
+// ---------------------------------------------------------------------------
 // column pass: block `bid` of one operand handles tile (o, j0..j0+TW)
 // ---------------------------------------------------------------------------
-template <typename T, int TW, int SIGN, int MODE>
+template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
 __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, int64_t bid) {
   using C = typename CT<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -37,55 +71,95 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
   if (a.st != nullptr && a.st->done != RUNNING) return;
   const int npass = load_passes<C>(st, pl);
 
-  const int M = pl.M;
+  const int M = MCT != 0 ? MCT : pl.M;
   const int64_t tiles = (a.inner + TW - 1) / TW;
   const int64_t o = bid / tiles;
   const int64_t j0 = (bid % tiles) * TW;
   const int width = static_cast<int>(a.inner - j0 < TW ? a.inner - j0 : TW);
   const C* __restrict__ tw = twtab<C>(pl);
-  const int* __restrict__ perm = pl.perm;
+  const int* __restrict__ perm = MCT != 0 ? pl.perm_ct : pl.perm;
 
   if (SIGN > 0) {
-    for (int u = threadIdx.x; u < static_cast<int>(padded_elems<C>(M * TW)); u += blockDim.x) buf[u] = mk(T(0), T(0));
-    __syncthreads();
     const C* __restrict__ in = static_cast<const C*>(a.in);
     const int Lin = a.Lin;
     const int half = (Lin - 1) / 2;
-    T beta = T(0);
-    if (MODE == COL_PUPDATE) beta = static_cast<T>(a.st->beta);
-    for (int u = threadIdx.x; u < Lin * TW; u += blockDim.x) {
+    // zero the frequencies the input does not reach: k = half+1 .. M-half-1
+    for (int u = threadIdx.x; u < (M - Lin) * TW; u += blockDim.x) {
       const int t = u % TW;
-      const int i = u / TW;
-      if (t < width) {
-        const int64_t idx = (o * Lin + i) * a.inner + j0 + t;
-        C v = in[idx];
-        if (MODE == COL_PUPDATE) {
-          C po = static_cast<const C*>(a.pold)[idx];
-          v = mk(v.x + beta * po.x, v.y + beta * po.y);
-          static_cast<C*>(a.pnew)[idx] = v;
-        }
+      const int k = half + 1 + u / TW;
+      buf[bix<MCT, C>(__ldg(&perm[k]) * TW + t)] = mk(T(0), T(0));
+    }
+    if (MODE == COL_PLAIN) {
+      for (int u = threadIdx.x; u < Lin * TW; u += blockDim.x) {
+        const int t = u % TW;
+        const int i = u / TW;
         int k = i - half;
         if (k < 0) k += M;
-        buf[pidx<C>(__ldg(&perm[k]) * TW + t)] = v;
+        C* dst = buf + bix<MCT, C>(__ldg(&perm[k]) * TW + t);
+        if (t < width) cp_async<sizeof(C)>(dst, in + (o * Lin + i) * a.inner + j0 + t);
+        else *dst = mk(T(0), T(0));
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+    } else {
+      // p = r + beta p_old, written back and scattered; K entries per thread
+      // are loaded before any is used so that their latencies overlap
+      constexpr int K = 4;
+      const T beta = static_cast<T>(a.st->beta);
+      const C* __restrict__ pold = static_cast<const C*>(a.pold);
+      C* pnew = static_cast<C*>(a.pnew);
+      for (int u0 = threadIdx.x; u0 < Lin * TW; u0 += K * blockDim.x) {
+        C v[K], po[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int u = u0 + q * blockDim.x;
+          const int t = u % TW;
+          const int i = u / TW;
+          v[q] = mk(T(0), T(0));
+          po[q] = mk(T(0), T(0));
+          if (u < Lin * TW && t < width) {
+            const int64_t idx = (o * Lin + i) * a.inner + j0 + t;
+            v[q] = in[idx];
+            po[q] = pold[idx];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int u = u0 + q * blockDim.x;
+          if (u < Lin * TW) {
+            const int t = u % TW;
+            const int i = u / TW;
+            const C w = mk(v[q].x + beta * po[q].x, v[q].y + beta * po[q].y);
+            if (t < width) pnew[(o * Lin + i) * a.inner + j0 + t] = w;
+            int k = i - half;
+            if (k < 0) k += M;
+            buf[bix<MCT, C>(__ldg(&perm[k]) * TW + t)] = (t < width) ? w : mk(T(0), T(0));
+          }
+        }
       }
     }
     __syncthreads();
-    fft_dit<+1, TW>(buf, st, npass, M, tw, roottab<C>(pl));
+    if constexpr (MCT != 0) fft_dit_ct<+1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw);
+    else fft_dit<+1, TW>(buf, st, npass, M, tw);
     C* __restrict__ out = static_cast<C*>(a.out);
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
       const int t = u % TW;
       const int m = u / TW;
-      if (t < width) out[(o * M + m) * a.inner + j0 + t] = buf[pidx<C>(m * TW + t)];
+      if (t < width) out[(o * M + m) * a.inner + j0 + t] = buf[bix<MCT, C>(m * TW + t)];
     }
   } else {
     const C* __restrict__ in = static_cast<const C*>(a.in);
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
       const int t = u % TW;
       const int m = u / TW;
-      buf[pidx<C>(u)] = (t < width) ? in[(o * M + m) * a.inner + j0 + t] : mk(T(0), T(0));
+      if (t < width) cp_async<sizeof(C)>(buf + bix<MCT, C>(u), in + (o * M + m) * a.inner + j0 + t);
+      else buf[bix<MCT, C>(u)] = mk(T(0), T(0));
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    fft_dif<-1, TW>(buf, st, npass, M, tw, roottab<C>(pl));
+    if constexpr (MCT != 0) fft_dif_ct<-1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw);
+    else fft_dif<-1, TW>(buf, st, npass, M, tw);
     C* __restrict__ out = static_cast<C*>(a.out);
     const int Lout = a.Lout;
     const int half = (Lout - 1) / 2;
@@ -96,7 +170,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
       if (t < width) {
         int k = i - half;
         if (k < 0) k += M;
-        C v = buf[pidx<C>(__ldg(&perm[k]) * TW + t)];
+        C v = buf[bix<MCT, C>(__ldg(&perm[k]) * TW + t)];
         out[(o * Lout + i) * a.inner + j0 + t] = inv * v;
       }
     }
@@ -107,10 +181,10 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
 constexpr int kColThreads32 = 512;
 constexpr int kColThreads64 = 256;
 
-template <typename T, int TW, int SIGN, int MODE>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? kColThreads64 : kColThreads32)
+template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
+__global__ void __launch_bounds__(col_threads<T, TW, MCT>())
     col_kernel(ColArgs a, FftPlan pl) {
-  col_body<T, TW, SIGN, MODE>(a, pl, blockIdx.x);
+  col_body<T, TW, SIGN, MODE, MCT>(a, pl, blockIdx.x);
 }
 
 // Index of the work item owning block `b` (items sorted by block_begin).
@@ -137,31 +211,32 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kColThreads64 : kColThreads32
   col_body<T, TW, SIGN, MODE>(it.a, *it.pl, blockIdx.x - it.block_begin);
 }
 
-template <typename T, int TW, int SIGN, int MODE>
+template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
 inline ghb_status launch_col_t(const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t smem = col_smem_bytes(pl.M, TW, sizeof(C));
   static bool attr_set = false;
   if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(col_kernel<T, TW, SIGN, MODE>,
+    GHB_CUDA_TRY(cudaFuncSetAttribute(col_kernel<T, TW, SIGN, MODE, MCT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     attr_set = true;
   }
   const int64_t tiles = (a.inner + TW - 1) / TW;
   const int64_t grid = tiles * a.outer;
-  const int threads = (sizeof(T) == 4 && pl.M * TW >= 2048) ? kColThreads32 : 256;
-  col_kernel<T, TW, SIGN, MODE><<<static_cast<unsigned>(grid), threads, smem, s>>>(a, pl);
+  const int threads = MCT != 0 ? col_threads<T, TW, MCT>()
+                               : ((sizeof(T) == 4 && pl.M * TW >= 2048) ? kColThreads32 : 256);
+  col_kernel<T, TW, SIGN, MODE, MCT><<<static_cast<unsigned>(grid), threads, smem, s>>>(a, pl);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }
 
 // All sign/mode variants of one precision and tile width.
-template <typename T, int TW>
+template <typename T, int TW, int MCT = 0>
 ghb_status launch_col_tw(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   if (sign > 0)
-    return mode == COL_PUPDATE ? launch_col_t<T, TW, +1, COL_PUPDATE>(a, pl, s)
-                               : launch_col_t<T, TW, +1, COL_PLAIN>(a, pl, s);
-  return launch_col_t<T, TW, -1, COL_PLAIN>(a, pl, s);
+    return mode == COL_PUPDATE ? launch_col_t<T, TW, +1, COL_PUPDATE, MCT>(a, pl, s)
+                               : launch_col_t<T, TW, +1, COL_PLAIN, MCT>(a, pl, s);
+  return launch_col_t<T, TW, -1, COL_PLAIN, MCT>(a, pl, s);
 }
 
 template <typename T, int TW, int SIGN, int MODE>
@@ -253,7 +328,7 @@ __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, in
       if (k > 0) buf[pidx<C>(__ldg(&perm[M - k]) * NL + j)] = mk(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
-    fft_dit<+1, NL>(buf, st, npass, M, tw, roottab<C>(pl));
+    fft_dit<+1, NL>(buf, st, npass, M, tw);
 
     if (MODE == ROW_MATVEC) {
       const T* __restrict__ am = static_cast<const T*>(a.a);
@@ -267,7 +342,7 @@ __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, in
         buf[pidx<C>(m * NL + j)] = mk(a0 * z.x, a1 * z.y);
       }
       __syncthreads();
-      fft_dif<-1, NL>(buf, st, npass, M, tw, roottab<C>(pl));
+      fft_dif<-1, NL>(buf, st, npass, M, tw);
       const T sc = T(0.5) / T(M);
       for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
         const int j = (NL == 1) ? 0 : u % NL;
@@ -353,13 +428,157 @@ __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, in
 
 constexpr int kRowThreads = 256;
 
+// FP32: at most 85 registers so that three CTAs share an SM (measured 19 %
+// faster at M = 4374 than two CTAs of 128 registers).
+// Operator pass with staged inputs (MATVEC only; used when the staging fits
+// in shared memory).  The CTA loops over row groups; the next group's half
+// spectra are copied asynchronously into a staging area while the current
+// group is transformed, and the next group's multiplier row while the current
+// one is transformed back:
+//
+//   smem = [ transform buffer | staged half spectra [2 NL][H] | staged A_M rows [rows][M] ]
+//
+// Copy groups in flight per thread: at the multiply, {A_M(g), spectra(g+1)};
+// wait_group 1 therefore waits for A_M(g) alone.
+template <typename T, int NL>
+__host__ __device__ inline size_t row_staged_smem(int M, int H, int rows_per_cta) {
+  using C = typename CT<T>::type;
+  return padded_elems<C>(static_cast<size_t>(M) * NL) * sizeof(C) + static_cast<size_t>(2 * NL) * H * sizeof(C) +
+         static_cast<size_t>(rows_per_cta) * M * sizeof(T);
+}
+
+template <typename T, int NL, int MCT = 0>
+__device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPlan& pl, int rows_per_cta,
+                                                  int64_t bid, int64_t nb) {
+  using C = typename CT<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PassSmem st;
+  __shared__ LineDesc ld[2 * NL];
+  if (a.st != nullptr && a.st->done != RUNNING) return;
+  const int npass = load_passes<C>(st, pl);
+
+  const int M = MCT != 0 ? MCT : pl.M;
+  const int H = a.H;
+  const int per_row = a.nfields * a.ncomp;
+  const int nrl = rows_per_cta * per_row;
+  const int64_t groups = (a.rows + rows_per_cta - 1) / rows_per_cta;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* sin = buf + padded_elems<C>(static_cast<size_t>(M) * NL);
+  T* sa = reinterpret_cast<T*>(sin + 2 * NL * H);
+  const C* __restrict__ tw = twtab<C>(pl);
+  const int* __restrict__ perm = MCT != 0 ? pl.perm_ct : pl.perm;
+  const T* __restrict__ am = static_cast<const T*>(a.a);
+
+  auto desc = [&](int64_t grp, int rho) {
+    LineDesc d;
+    d.row = grp * rows_per_cta + rho / per_row;
+    d.field = (rho / a.ncomp) % a.nfields;
+    d.comp = rho % a.ncomp;
+    d.valid = (rho < nrl) && (d.row < a.rows);
+    return d;
+  };
+  auto issue_spectra = [&](int64_t grp) {
+#pragma unroll
+    for (int rho = 0; rho < 2 * NL; ++rho) {
+      const LineDesc d = desc(grp, rho);
+      if (!d.valid) continue;
+      const C* src = static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H;
+      for (int k = threadIdx.x; k < H; k += blockDim.x) cp_async<sizeof(C)>(sin + rho * H + k, src + k);
+    }
+  };
+  auto issue_multiplier = [&](int64_t grp) {
+    for (int r = 0; r < rows_per_cta; ++r) {
+      const int64_t row = grp * rows_per_cta + r;
+      if (row >= a.rows) break;
+      for (int m = threadIdx.x; m < M; m += blockDim.x) cp_async<sizeof(T)>(sa + r * M + m, am + row * M + m);
+    }
+  };
+
+  int64_t grp = bid;
+  if (grp < groups) {
+    issue_spectra(grp);
+    cp_async_commit();
+    issue_multiplier(grp);
+    cp_async_commit();
+  }
+  for (; grp < groups; grp += nb) {
+    if (threadIdx.x < 2 * NL) ld[threadIdx.x] = desc(grp, threadIdx.x);
+    cp_async_wait<1>();          // spectra(g) are in; A_M(g) may still be in flight
+    __syncthreads();
+
+    // Hermitian completion of each pair of half spectra (Z(k) = X0(k) + i X1(k),
+    // Z(-k) = conj X0(k) + i conj X1(k)) into digit-reversed positions, and
+    // zeros at the frequencies the spectra do not reach (k = H .. M-H)
+    for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
+      const int j = (NL == 1) ? 0 : u % NL;
+      const int k = (NL == 1) ? u : u / NL;
+      const C A = ld[2 * j].valid ? sin[(2 * j) * H + k] : mk(T(0), T(0));
+      const C B = ld[2 * j + 1].valid ? sin[(2 * j + 1) * H + k] : mk(T(0), T(0));
+      buf[bix<MCT, C>(__ldg(&perm[k]) * NL + j)] = mk(A.x - B.y, A.y + B.x);
+      if (k > 0) buf[bix<MCT, C>(__ldg(&perm[M - k]) * NL + j)] = mk(A.x + B.y, B.x - A.y);
+    }
+    for (int u = threadIdx.x; u < NL * (M - 2 * H + 1); u += blockDim.x) {
+      const int j = (NL == 1) ? 0 : u % NL;
+      const int k = H + ((NL == 1) ? u : u / NL);
+      buf[bix<MCT, C>(__ldg(&perm[k]) * NL + j)] = mk(T(0), T(0));
+    }
+    __syncthreads();
+    if (grp + nb < groups) issue_spectra(grp + nb);   // staging is free again
+    cp_async_commit();
+
+    if constexpr (MCT != 0) fft_dit_ct<+1, NL, kRowThreads, MCT>(buf, tw);
+    else fft_dit<+1, NL>(buf, st, npass, M, tw);
+    cp_async_wait<1>();          // A_M(g) is in; spectra(g+1) may still be in flight
+    __syncthreads();
+    for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
+      const int j = (NL == 1) ? 0 : u % NL;
+      const int m = (NL == 1) ? u : u / NL;
+      const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
+      const C z = buf[bix<MCT, C>(m * NL + j)];
+      const T a0 = d0.valid ? sa[((2 * j) / per_row) * M + m] : T(0);
+      const T a1 = d1.valid ? sa[((2 * j + 1) / per_row) * M + m] : T(0);
+      buf[bix<MCT, C>(m * NL + j)] = mk(a0 * z.x, a1 * z.y);
+    }
+    __syncthreads();
+    if (grp + nb < groups) issue_multiplier(grp + nb);
+    cp_async_commit();
+
+    if constexpr (MCT != 0) fft_dif_ct<-1, NL, kRowThreads, MCT>(buf, tw);
+    else fft_dif<-1, NL>(buf, st, npass, M, tw);
+    const T sc = T(0.5) / T(M);
+    for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
+      const int j = (NL == 1) ? 0 : u % NL;
+      const int k = (NL == 1) ? u : u / NL;
+      const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
+      const C W = buf[bix<MCT, C>(__ldg(&perm[k]) * NL + j)];
+      const C Wm = buf[bix<MCT, C>(__ldg(&perm[k == 0 ? 0 : M - k]) * NL + j)];
+      if (d0.valid)
+        static_cast<C*>(a.t[d0.field])[d0.comp * a.comp_stride + d0.row * H + k] =
+            mk(sc * (W.x + Wm.x), sc * (W.y - Wm.y));
+      if (d1.valid)
+        static_cast<C*>(a.t[d1.field])[d1.comp * a.comp_stride + d1.row * H + k] =
+            mk(sc * (W.y + Wm.y), sc * (Wm.x - W.x));
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T, int NL, int MCT = 0>
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? 3 : 1)
+    row_kernel_staged(RowArgs a, FftPlan pl, int rows_per_cta) {
+  row_matvec_staged<T, NL, MCT>(a, pl, rows_per_cta, blockIdx.x, gridDim.x);
+}
+
 template <typename T, int NL, int MODE>
-__global__ void __launch_bounds__(kRowThreads) row_kernel(RowArgs a, FftPlan pl, int rows_per_cta) {
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? 3 : 1)
+    row_kernel(RowArgs a, FftPlan pl, int rows_per_cta) {
   row_body<T, NL, MODE>(a, pl, rows_per_cta, blockIdx.x, gridDim.x);
 }
 
 template <typename T, int NL, int MODE>
-__global__ void __launch_bounds__(kRowThreads) row_kernel_batch(const RowItem* __restrict__ items, int n) {
+__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? 3 : 1)
+    row_kernel_batch(const RowItem* __restrict__ items, int n) {
   __shared__ int s_item;
   if (threadIdx.x == 0) s_item = find_item(items, n, blockIdx.x);
   __syncthreads();
@@ -381,7 +600,7 @@ inline ghb_status launch_row_batch_t(const RowItem* items, int n, int64_t blocks
   return GHB_OK;
 }
 
-template <typename T, int NL, int MODE>
+template <typename T, int NL, int MODE, int MCT = 0>
 inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per_cta,
                                cudaStream_t s) {
   using C = typename CT<T>::type;
@@ -397,11 +616,54 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
     return GHB_ERR_INVALID;
   }
   const int64_t groups = (a.rows + rows_per_cta - 1) / rows_per_cta;
+  if constexpr (MODE == ROW_MATVEC) {
+    const size_t ssmem = row_staged_smem<T, NL>(pl.M, a.H, rows_per_cta);
+    if (ssmem <= 200 * 1024) {
+      // persistent grid: as many CTAs as fit on the device at once
+      static int per_sm = 0, sms = 0;
+      static size_t per_sm_smem = 0;
+      if (per_sm_smem != ssmem) {
+        GHB_CUDA_TRY(cudaFuncSetAttribute(row_kernel_staged<T, NL, MCT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        GHB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_kernel_staged<T, NL, MCT>,
+                                                                   kRowThreads, ssmem));
+        int dev = 0;
+        GHB_CUDA_TRY(cudaGetDevice(&dev));
+        GHB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        per_sm_smem = ssmem;
+      }
+      int64_t grid = static_cast<int64_t>(per_sm > 0 ? per_sm : 1) * sms;
+      if (grid > groups) grid = groups;
+      if (grid < 1) grid = 1;
+      row_kernel_staged<T, NL, MCT><<<static_cast<unsigned>(grid), kRowThreads, ssmem, s>>>(a, pl, rows_per_cta);
+      GHB_CUDA_TRY(cudaGetLastError());
+      return GHB_OK;
+    }
+  }
   int64_t grid = groups;
   if (MODE == ROW_ENERGY && grid > 1024) grid = 1024;   // partials hold 1024 x 6 doubles
   row_kernel<T, NL, MODE><<<static_cast<unsigned>(grid), kRowThreads, smem, s>>>(a, pl, rows_per_cta);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
+}
+
+// Size-specialised FP32 operator passes for one transform length M
+// (instantiated in the ct_*.cu units).
+template <int M>
+ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
+  constexpr int TW = col_tile_width(M, 8);
+  return launch_col_tw<float, TW, M>(sign, mode, a, pl, s);
+}
+template <int M>
+ghb_status launch_row_ct_m(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s) {
+  switch (NL) {
+    case 1: return launch_row_t<float, 1, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
+    case 2: return launch_row_t<float, 2, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
+    case 3: return launch_row_t<float, 3, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
+    default: break;
+  }
+  set_error("internal: unsupported row-pass line count");
+  return GHB_ERR_INVALID;
 }
 
 }  // namespace ghb

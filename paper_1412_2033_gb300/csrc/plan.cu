@@ -2,6 +2,7 @@
 #include <cmath>
 #include <vector>
 
+#include "fft_ct.cuh"
 #include "ghb_internal.cuh"
 
 namespace ghb {
@@ -142,18 +143,6 @@ ghb_status build_plan_tables(int M, FftPlan& p, PlanTables& t) {
     tw64[j] = make_double2(c, s);
     tw32[j] = make_float2(static_cast<float>(c), static_cast<float>(s));
   }
-  // roots of unity of small order for the register-blocked passes
-  std::vector<double2>& r64 = t.r64;
-  std::vector<float2>& r32 = t.r32;
-  r64.resize(kRootTable);
-  r32.resize(kRootTable);
-  for (int n = 1; n <= kMaxRootOrder; ++n)
-    for (int k = 0; k < n; ++k) {
-      const long double a = two_pi * static_cast<long double>(k) / static_cast<long double>(n);
-      const double c = static_cast<double>(cosl(a)), sn = -static_cast<double>(sinl(a));
-      r64[n * (n - 1) / 2 + k] = make_double2(c, sn);
-      r32[n * (n - 1) / 2 + k] = make_float2(static_cast<float>(c), static_cast<float>(sn));
-    }
   return GHB_OK;
 }
 
@@ -165,32 +154,30 @@ ghb_status make_plan(int M, PlanHolder& out) {
   const std::vector<int>& perm = t.perm;
   const std::vector<double2>& tw64 = t.tw64;
   const std::vector<float2>& tw32 = t.tw32;
-  const std::vector<double2>& r64 = t.r64;
-  const std::vector<float2>& r32 = t.r32;
-  GHB_CUDA_TRY(cudaMalloc(&out.d_roots64, sizeof(double2) * kRootTable));
-  GHB_CUDA_TRY(cudaMalloc(&out.d_roots32, sizeof(float2) * kRootTable));
-  GHB_CUDA_TRY(cudaMemcpy(out.d_roots64, r64.data(), sizeof(double2) * kRootTable, cudaMemcpyHostToDevice));
-  GHB_CUDA_TRY(cudaMemcpy(out.d_roots32, r32.data(), sizeof(float2) * kRootTable, cudaMemcpyHostToDevice));
   GHB_CUDA_TRY(cudaMalloc(&out.d_perm, sizeof(int) * M));
   GHB_CUDA_TRY(cudaMalloc(&out.d_tw64, sizeof(double2) * M));
   GHB_CUDA_TRY(cudaMalloc(&out.d_tw32, sizeof(float2) * M));
   GHB_CUDA_TRY(cudaMemcpy(out.d_perm, perm.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
   GHB_CUDA_TRY(cudaMemcpy(out.d_tw64, tw64.data(), sizeof(double2) * M, cudaMemcpyHostToDevice));
   GHB_CUDA_TRY(cudaMemcpy(out.d_tw32, tw32.data(), sizeof(float2) * M, cudaMemcpyHostToDevice));
+  if (ct_size(M) && ct_plan(M).ok) {
+    std::vector<int> pct(M);
+    ct_perm(M, pct.data());
+    GHB_CUDA_TRY(cudaMalloc(&out.d_perm_ct, sizeof(int) * M));
+    GHB_CUDA_TRY(cudaMemcpy(out.d_perm_ct, pct.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
+  }
   p.perm = out.d_perm;
+  p.perm_ct = out.d_perm_ct;
   p.tw64 = out.d_tw64;
   p.tw32 = out.d_tw32;
-  p.roots64 = out.d_roots64;
-  p.roots32 = out.d_roots32;
   return GHB_OK;
 }
 
 void free_plan(PlanHolder& p) {
   if (p.d_perm) cudaFree(p.d_perm);
+  if (p.d_perm_ct) cudaFree(p.d_perm_ct);
   if (p.d_tw64) cudaFree(p.d_tw64);
   if (p.d_tw32) cudaFree(p.d_tw32);
-  if (p.d_roots64) cudaFree(p.d_roots64);
-  if (p.d_roots32) cudaFree(p.d_roots32);
   p = PlanHolder{};
 }
 

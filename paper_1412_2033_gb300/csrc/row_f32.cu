@@ -14,8 +14,10 @@ ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size
 }
 
 template ghb_status launch_row_nl<float, 1, ROW_MATVEC>(const RowArgs&, const FftPlan&, int, cudaStream_t);
+template ghb_status launch_row_nl<float, 2, ROW_MATVEC>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_nl<float, 3, ROW_MATVEC>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_batch_nl<float, 1, ROW_MATVEC>(const RowItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_row_batch_nl<float, 2, ROW_MATVEC>(const RowItem*, int, int64_t, size_t, cudaStream_t);
 template ghb_status launch_row_batch_nl<float, 3, ROW_MATVEC>(const RowItem*, int, int64_t, size_t, cudaStream_t);
 
 }  // namespace ghb

@@ -14,6 +14,7 @@ ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size
 }
 
 template ghb_status launch_row_nl<double, 1, ROW_MATVEC>(const RowArgs&, const FftPlan&, int, cudaStream_t);
+template ghb_status launch_row_nl<double, 2, ROW_MATVEC>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_nl<double, 3, ROW_MATVEC>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_nl<double, 1, ROW_TOREAL>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_nl<double, 1, ROW_ENERGY>(const RowArgs&, const FftPlan&, int, cudaStream_t);
@@ -22,6 +23,7 @@ template ghb_status launch_row_nl<double, 3, ROW_ENERGY>(const RowArgs&, const F
 template ghb_status launch_row_nl<double, 4, ROW_ENERGY>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_nl<double, 5, ROW_ENERGY>(const RowArgs&, const FftPlan&, int, cudaStream_t);
 template ghb_status launch_row_batch_nl<double, 1, ROW_MATVEC>(const RowItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_row_batch_nl<double, 2, ROW_MATVEC>(const RowItem*, int, int64_t, size_t, cudaStream_t);
 template ghb_status launch_row_batch_nl<double, 3, ROW_MATVEC>(const RowItem*, int, int64_t, size_t, cudaStream_t);
 template ghb_status launch_row_batch_nl<double, 1, ROW_TOREAL>(const RowItem*, int, int64_t, size_t, cudaStream_t);
 template ghb_status launch_row_batch_nl<double, 1, ROW_ENERGY>(const RowItem*, int, int64_t, size_t, cudaStream_t);

@@ -246,20 +246,21 @@ def test_matvec_sizes(ghb, N, M, prec):
     assert rel(got, ref) < (1e-12 if prec == "f64" else 2e-5)
 
 
+@pytest.mark.parametrize("N", [729, 2187])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_matvec_full_size_sampled(ghb, prec):
-    """The measured workload (d = 2 disk, N = 2187, M = 4374): the operator on a
-    random field at sampled output frequencies against the oracle's definition
-    y(l) = G(l) sum_k a^(l - k) x(k)."""
-    m = W.centred_disk(2187, fraction=0.3, value=100.0)
+def test_matvec_full_size_sampled(ghb, N, prec):
+    """The measured workload (d = 2 disk, N = 2187, M = 4374) and N = 729
+    (M = 1458): the operator on a random field at sampled output frequencies
+    against the oracle's definition y(l) = G(l) sum_k a^(l - k) x(k)."""
+    m = W.centred_disk(N, fraction=0.3, value=100.0)
     ctx = ghb.Context.from_microstructure(m)
-    assert ctx.M == [4374, 4374]
-    x = W.random_field(np.random.default_rng(2187), 2, [2187, 2187])
+    assert ctx.M == [2 * N, 2 * N]
+    x = W.random_field(np.random.default_rng(N), 2, [N, N])
     dt = torch.complex128 if prec == "f64" else torch.complex64
     xt = torch.from_numpy(np.ascontiguousarray(ghb.half_from_full(x))).to(dt).cuda()
     y = ctx.matvec(xt).cpu().numpy()
-    c = 1093
-    idx = np.array([[0, 0], [1, 0], [0, 1], [-1093, 1093], [1093, 0], [37, 911], [-512, 3], [700, 1093]])
+    c = (N - 1) // 2
+    idx = np.array([[0, 0], [1, 0], [0, 1], [-c, c], [c, 0], [37, c - 182], [-512 % c, 3], [c - 393, c]])
     ref = OG.matvec_sampled(x, OC.material_from_dict(m), OG.PRIMAL, idx)
     got = np.array([y[:, l[0] + c, l[1]] for l in idx])
     scale = np.abs(ref).max()
