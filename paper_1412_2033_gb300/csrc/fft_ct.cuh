@@ -18,6 +18,8 @@
 // table built by ct_perm (not the runtime plan's).
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace ghb {
@@ -126,10 +128,58 @@ __device__ __forceinline__ void ct_substage(C* v, int p, const C* __restrict__ t
   }
 }
 
+// Natural index of the entries of the first pass (L_{t-1} = 1).  Its unit b
+// holds positions b RG + j, j = d1 + RA d2 + RA RB d3, which carry the input
+// (DIT) or output (DIF) index
+//     n = rest(b) + (M / RG) (d1 RB RC + d2 RC + d3),
+// rest(b) = the remaining position digits of b, each weighted by the product of
+// the radices of the stages after its own.
+template <int RA, int RB, int RC>
+__host__ __device__ constexpr int ct_revj(int j) {
+  return (j % RA) * RB * RC + ((j / RA) % RB) * RC + j / (RA * RB);
+}
+__host__ __device__ constexpr int ct_weight(int M, int t) {   // product of the radices after stage t
+  int w = 1;
+  for (int u = t + 1; u < ct_plan(M).nst; ++u) w *= ct_plan(M).R[u];
+  return w;
+}
+template <int M, int T>
+__device__ __forceinline__ int ct_rest_from(int b) {
+  constexpr CtPlan P = ct_plan(M);
+  if constexpr (T >= P.nst) {
+    return 0;
+  } else {
+    constexpr int R = P.R[T];
+    constexpr int W = ct_weight(M, T);
+    return (b % R) * W + ct_rest_from<M, T + 1>(b / R);
+  }
+}
+template <int M>
+__device__ __forceinline__ int ct_rest(int b) {
+  constexpr CtPlan P = ct_plan(M);
+  constexpr int s0 = (P.ra[0] > 1) + (P.rb[0] > 1) + (P.rc[0] > 1);
+  return ct_rest_from<M, s0>(b);
+}
+// Placeholder for "read from / write to the shared buffer".
+struct CtBuf {};
+
+// Sources with a member kWriteBack = true also get write_back(line, n, value)
+// for every entry, called after all of a unit's entries have been read.
+template <typename S, typename = void>
+struct ct_writes_back : std::false_type {};
+template <typename S>
+struct ct_writes_back<S, std::void_t<decltype(S::kWriteBack)>> : std::integral_constant<bool, S::kWriteBack> {};
+
 // One pass: butterflies of radix RA RB RC on stride LP, NT threads, NL lines
-// interleaved (element (m, line) at m NL + line, no padding).
-template <int SIGN, bool DIT, int NL, int NT, int M, int LP, int RA, int RB, int RC, typename C>
-__device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw) {
+// interleaved (element (m, line) at m NL + line, no padding).  The first pass
+// may take its entries from a source instead of the buffer (DIT: src(line, n)
+// returns input n, so the caller's scatter into digit-reversed order and its
+// zero padding disappear) and may hand its results to a sink instead of the
+// buffer (DIF: snk(line, n, value) receives output n).
+template <int SIGN, bool DIT, int NL, int NT, int M, int LP, int RA, int RB, int RC, typename C,
+          typename Src = CtBuf, typename Snk = CtBuf>
+__device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw, const Src& src = Src(),
+                                        const Snk& snk = Snk()) {
   constexpr int RG = RA * RB * RC;
   constexpr int units = M / RG;
   constexpr int total = units * NL;
@@ -138,6 +188,9 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw) {
   constexpr int tsC = tsB / RC;
   constexpr int step = LP * NL;
   constexpr bool FIRST = (LP == 1);
+  constexpr bool FROM_SRC = !std::is_same<Src, CtBuf>::value;
+  constexpr bool TO_SNK = !std::is_same<Snk, CtBuf>::value;
+  static_assert(FIRST || (!FROM_SRC && !TO_SNK), "sources and sinks belong to the first pass");
 #pragma unroll 1
   for (int u = threadIdx.x; u < total; u += NT) {
     const int line = (NL == 1) ? 0 : u % NL;
@@ -145,9 +198,19 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw) {
     const int b = unit / LP;
     const int p = unit - b * LP;
     C* base = buf + (b * LP * RG + p) * NL + line;
+    int nb = 0;
+    if constexpr (FROM_SRC || TO_SNK) nb = ct_rest<M>(b);
     C v[RG];
 #pragma unroll
-    for (int j = 0; j < RG; ++j) v[j] = base[j * step];
+    for (int j = 0; j < RG; ++j) {
+      if constexpr (FROM_SRC) v[j] = src(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j));
+      else v[j] = base[j * step];
+    }
+    if constexpr (FROM_SRC && ct_writes_back<Src>::value) {
+      // a source that also stores what it produced does so after all its loads
+#pragma unroll
+      for (int j = 0; j < RG; ++j) src.write_back(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j), v[j]);
+    }
     if constexpr (DIT) {
       ct_substage<SIGN, DIT, FIRST, RA, 1, RG, tsA>(v, p, tw);
       if constexpr (RB > 1) ct_substage<SIGN, DIT, FIRST, RB, RA, RG, tsB>(v, p, tw);
@@ -158,7 +221,10 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw) {
       ct_substage<SIGN, DIT, FIRST, RA, 1, RG, tsA>(v, p, tw);
     }
 #pragma unroll
-    for (int j = 0; j < RG; ++j) base[j * step] = v[j];
+    for (int j = 0; j < RG; ++j) {
+      if constexpr (TO_SNK) snk(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j), v[j]);
+      else base[j * step] = v[j];
+    }
   }
 }
 
@@ -172,13 +238,13 @@ __device__ __forceinline__ void ct_dit_from(C* buf, const C* __restrict__ tw) {
   }
 }
 
-template <int SIGN, int NL, int NT, int M, int I, typename C>
+template <int SIGN, int NL, int NT, int M, int I, int LO = 0, typename C>
 __device__ __forceinline__ void ct_dif_from(C* buf, const C* __restrict__ tw) {
   constexpr CtPlan P = ct_plan(M);
-  if constexpr (I >= 0) {
+  if constexpr (I >= LO) {
     ct_pass<SIGN, false, NL, NT, M, P.lp[I], P.ra[I], P.rb[I], P.rc[I]>(buf, tw);
     __syncthreads();
-    ct_dif_from<SIGN, NL, NT, M, I - 1>(buf, tw);
+    ct_dif_from<SIGN, NL, NT, M, I - 1, LO>(buf, tw);
   }
 }
 
@@ -190,11 +256,33 @@ __device__ __forceinline__ void fft_dit_ct(C* buf, const C* __restrict__ tw) {
   ct_dit_from<SIGN, NL, NT, M, 0>(buf, tw);
 }
 
+// The same with the input read from src(line, n), n the natural index (no
+// scatter into buf beforehand; the first pass reads src and writes buf).
+template <int SIGN, int NL, int NT, int M, typename C, typename Src>
+__device__ __forceinline__ void fft_dit_ct_src(C* buf, const C* __restrict__ tw, const Src& src) {
+  constexpr CtPlan P = ct_plan(M);
+  static_assert(P.ok, "transform length must factor into 2, 3, 4, 5");
+  ct_pass<SIGN, true, NL, NT, M, 1, P.ra[0], P.rb[0], P.rc[0]>(buf, tw, src);
+  __syncthreads();
+  ct_dit_from<SIGN, NL, NT, M, 1>(buf, tw);
+}
+
 // Decimation in frequency: natural input -> digit-reversed output.
 template <int SIGN, int NL, int NT, int M, typename C>
 __device__ __forceinline__ void fft_dif_ct(C* buf, const C* __restrict__ tw) {
   static_assert(ct_plan(M).ok, "transform length must factor into 2, 3, 4, 5");
   ct_dif_from<SIGN, NL, NT, M, ct_plan(M).npass - 1>(buf, tw);
+}
+
+// The same with every output handed to snk(line, n, value), n the natural
+// index, instead of being stored (the last pass reads buf and calls snk; buf
+// is left partly overwritten).  Ends without a barrier.
+template <int SIGN, int NL, int NT, int M, typename C, typename Snk>
+__device__ __forceinline__ void fft_dif_ct_snk(C* buf, const C* __restrict__ tw, const Snk& snk) {
+  constexpr CtPlan P = ct_plan(M);
+  static_assert(P.ok, "transform length must factor into 2, 3, 4, 5");
+  ct_dif_from<SIGN, NL, NT, M, P.npass - 1, 1>(buf, tw);
+  ct_pass<SIGN, false, NL, NT, M, 1, P.ra[0], P.rb[0], P.rc[0], C, CtBuf, Snk>(buf, tw, CtBuf(), snk);
 }
 
 }  // namespace ghb

@@ -62,6 +62,45 @@ __host__ __device__ constexpr int col_threads() {
 // ---------------------------------------------------------------------------
 // column pass: block `bid` of one operand handles tile (o, j0..j0+TW)
 // ---------------------------------------------------------------------------
+// Input of the size-specialised inverse column transform: entry n of tile
+// line t is input row i(n) = n + half (n <= half) or n - M + half
+// (n >= M - half), zero in between; with UPDATE the entry is r + beta p_old
+// and is written back to p_new once all of a unit's entries are loaded.
+template <typename C, typename T, bool UPDATE>
+struct ColSource {
+  static constexpr bool kWriteBack = UPDATE;
+  const C* __restrict__ in;
+  const C* __restrict__ pold;
+  C* __restrict__ pnew;
+  T beta;
+  int64_t base;     // index of (row half, column j0) of this tile
+  int64_t inner;    // row stride
+  int half, M, width;
+  __device__ __forceinline__ int64_t index(int t, int n, bool& ok) const {
+    const int r = n <= half ? n : (n >= M - half ? n - M : M);   // row offset from the centre
+    ok = r != M && t < width;
+    return base + static_cast<int64_t>(r) * inner + t;
+  }
+  __device__ __forceinline__ C operator()(int t, int n) const {
+    bool ok;
+    const int64_t idx = index(t, n, ok);
+    C v = mk(T(0), T(0));
+    if (ok) {
+      v = in[idx];
+      if constexpr (UPDATE) {
+        const C po = pold[idx];
+        v = mk(v.x + beta * po.x, v.y + beta * po.y);
+      }
+    }
+    return v;
+  }
+  __device__ __forceinline__ void write_back(int t, int n, C v) const {
+    bool ok;
+    const int64_t idx = index(t, n, ok);
+    if (ok) pnew[idx] = v;
+  }
+};
+
 template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
 __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, int64_t bid) {
   using C = typename CT<T>::type;
@@ -79,7 +118,48 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
   const C* __restrict__ tw = twtab<C>(pl);
   const int* __restrict__ perm = MCT != 0 ? pl.perm_ct : pl.perm;
 
-  if (SIGN > 0) {
+  if constexpr (MCT != 0 && SIGN > 0) {
+    // The size-specialised transform reads its input rows straight from global
+    // memory in its first pass (input n of line t is row i(n) of the tile,
+    // zero outside the padded range; p = r + beta p_old is formed and written
+    // back on the way).
+    const C* __restrict__ in = static_cast<const C*>(a.in);
+    const int Lin = a.Lin;
+    const int half = (Lin - 1) / 2;
+    T beta = T(0);
+    if constexpr (MODE == COL_PUPDATE) beta = static_cast<T>(a.st->beta);
+    ColSource<C, T, MODE == COL_PUPDATE> src{in, static_cast<const C*>(a.pold), static_cast<C*>(a.pnew), beta,
+                                            (o * Lin + half) * a.inner + j0, a.inner, half, M, width};
+    fft_dit_ct_src<+1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, src);
+    C* __restrict__ out = static_cast<C*>(a.out);
+    for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
+      const int t = u % TW;
+      const int m = u / TW;
+      if (t < width) out[(o * M + m) * a.inner + j0 + t] = buf[m * TW + t];
+    }
+  } else if constexpr (MCT != 0) {
+    // forward, size-specialised: natural-order input copied in, the last
+    // pass hands the kept frequencies (scaled by 1/M) straight to global memory
+    const C* __restrict__ in = static_cast<const C*>(a.in);
+    for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
+      const int t = u % TW;
+      const int m = u / TW;
+      if (t < width) cp_async<sizeof(C)>(buf + u, in + (o * M + m) * a.inner + j0 + t);
+      else buf[u] = mk(T(0), T(0));
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    C* __restrict__ out = static_cast<C*>(a.out);
+    const int Lout = a.Lout;
+    const int half = (Lout - 1) / 2;
+    const T inv = T(1) / T(M);
+    auto snk = [&](int t, int n, C v) {
+      const int i = n <= half ? n + half : (n >= M - half ? n - M + half : -1);
+      if (i >= 0 && t < width) out[(o * Lout + i) * a.inner + j0 + t] = inv * v;
+    };
+    fft_dif_ct_snk<-1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, snk);
+  } else if (SIGN > 0) {
     const C* __restrict__ in = static_cast<const C*>(a.in);
     const int Lin = a.Lin;
     const int half = (Lin - 1) / 2;
@@ -139,8 +219,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
       }
     }
     __syncthreads();
-    if constexpr (MCT != 0) fft_dit_ct<+1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw);
-    else fft_dit<+1, TW>(buf, st, npass, M, tw);
+    fft_dit<+1, TW>(buf, st, npass, M, tw);
     C* __restrict__ out = static_cast<C*>(a.out);
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
       const int t = u % TW;
@@ -158,8 +237,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    if constexpr (MCT != 0) fft_dif_ct<-1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw);
-    else fft_dif<-1, TW>(buf, st, npass, M, tw);
+    fft_dif<-1, TW>(buf, st, npass, M, tw);
     C* __restrict__ out = static_cast<C*>(a.out);
     const int Lout = a.Lout;
     const int half = (Lout - 1) / 2;
@@ -508,7 +586,21 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
 
     // Hermitian completion of each pair of half spectra (Z(k) = X0(k) + i X1(k),
     // Z(-k) = conj X0(k) + i conj X1(k)) into digit-reversed positions, and
-    // zeros at the frequencies the spectra do not reach (k = H .. M-H)
+    // zeros at the frequencies the spectra do not reach (k = H .. M-H).  The
+    // size-specialised transform reads the completed spectrum directly in its
+    // first pass instead.
+    if constexpr (MCT != 0) {
+      auto src = [&](int j, int n) -> C {
+        const bool lo = n < H, hi = n > M - H;
+        const int k = lo ? n : M - n;
+        C A = mk(T(0), T(0)), B = mk(T(0), T(0));
+        if ((lo || hi) && ld[2 * j].valid) A = sin[(2 * j) * H + k];
+        if ((lo || hi) && ld[2 * j + 1].valid) B = sin[(2 * j + 1) * H + k];
+        return lo ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
+      };
+      fft_dit_ct_src<+1, NL, kRowThreads, MCT>(buf, tw, src);   // ends with a barrier
+      if (grp + nb < groups) issue_spectra(grp + nb);            // staging is free again
+    } else {
     for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
       const int k = (NL == 1) ? u : u / NL;
@@ -524,10 +616,10 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     }
     __syncthreads();
     if (grp + nb < groups) issue_spectra(grp + nb);   // staging is free again
+    fft_dit<+1, NL>(buf, st, npass, M, tw);
+    }
     cp_async_commit();
 
-    if constexpr (MCT != 0) fft_dit_ct<+1, NL, kRowThreads, MCT>(buf, tw);
-    else fft_dit<+1, NL>(buf, st, npass, M, tw);
     cp_async_wait<1>();          // A_M(g) is in; spectra(g+1) may still be in flight
     __syncthreads();
     for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
