@@ -276,6 +276,38 @@ void ghb_batch_destroy(ghb_batch* b);
 ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* grid_dev, int m,
                             const void* const* fields_dev, double* out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Launch configuration of the transform passes (no counterpart in the paper:
+ * it decides how the FFTs of Algorithm 2 are laid out on the GPU, not what
+ * they compute).  Per transform length M the library holds
+ *   cfg[0] cap32   largest radix product of one register-blocked pass of the
+ *                  runtime-plan FP32 transform (5..32)
+ *   cfg[1] tile32  columns per CTA of the FP32 column passes (0 = size rule,
+ *                  else 1, 2, 4, 8 or 16 within shared memory)
+ *   cfg[2] rows32  rows per CTA of the FP32 2-D last-axis pass (0 = size rule,
+ *                  1 or 2)
+ *   cfg[3] ct_col  1: size-specialised FP32 column kernels (only for lengths
+ *                  that have them: 162, 486, 1458, 4374), 0: runtime plan
+ *   cfg[4] ct_row  the same for the last-axis pass
+ *   cfg[5] cap64   as cap32 for FP64
+ *   cfg[6] tile64  as tile32 for FP64
+ * The first plan for M in a process times the candidates on a square 2-D
+ * operand with CUDA events and keeps the fastest (the autotuner); setting the
+ * environment variable GHB_AUTOTUNE=0 keeps the size rules instead.  Every
+ * configuration computes the same operator; results differ only by rounding.
+ * A configuration applies to plans made after it is fixed (contexts and batch
+ * instances created later).
+ *
+ * ghb_tune_get: cfg[7] host, receives M's configuration, tuning M first if it
+ *   has not been (this allocates and runs kernels on the current device).
+ * ghb_tune_set: fixes M's configuration to cfg[7] (validated; GHB_ERR_INVALID
+ *   with a message otherwise).
+ * ghb_tune_reset: forgets every stored configuration.
+ * All three are thread-safe; M must factor into primes <= 31. */
+ghb_status ghb_tune_get(int M, int* cfg);
+ghb_status ghb_tune_set(int M, const int* cfg);
+ghb_status ghb_tune_reset(void);
+
 /* Device bytes held by the context. */
 int64_t ghb_device_bytes(const ghb_ctx* ctx);
 

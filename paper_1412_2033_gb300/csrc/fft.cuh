@@ -101,6 +101,10 @@ struct FftPlan {
                              // size-specialised kernels)
   const double2* tw64;       // tw64[j] = exp(-2 pi i j / M)
   const float2* tw32;        // the same rounded to float
+  // launch configuration chosen by the autotuner (host-side choices; 0 = size rule)
+  int tile[2];               // column-pass tile width ([0] FP64, [1] FP32)
+  int rows32;                // rows per CTA of the FP32 2-D operator's last-axis pass
+  int ct_col, ct_row;        // 1: size-specialised FP32 kernels for the column / last-axis passes
 };
 
 template <typename T> struct CT;

@@ -85,7 +85,16 @@ struct PlanHolder {
   float2* d_tw32 = nullptr;
 };
 
+// Plan with tables on the device and the autotuned launch configuration
+// (make_plan) or the size rules (make_plan_untuned).
 ghb_status make_plan(int M, PlanHolder& out);
+ghb_status make_plan_untuned(int M, PlanHolder& out);
+// Regroup the stages of precision k ([0] FP64, [1] FP32) into passes of radix
+// product <= maxprod.
+void group_passes(FftPlan& p, int k, int maxprod);
+// Write the autotuned configuration for length M into p (tuning M first if
+// it has not been tuned in this process and tuning is enabled).
+ghb_status apply_tune(int M, FftPlan& p);
 // Host tables of a plan (digit reversal, twiddles); the
 // plan's device pointers are left null for the caller to place the tables.
 struct PlanTables {
@@ -170,11 +179,9 @@ template <typename T>
 ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem,
                             cudaStream_t s);
 // rows per CTA and interleaved complex lines of a row pass
-void row_lines(int mode, int nfields, int ncomp, int* rows_per_cta, int* NL);
-// 1 or 2 rows per CTA in the d = 2 operator's last-axis pass (0 = by size)
-void set_matvec_rows(int r);
-// transform length the next row_lines call plans for (batched launches)
-void set_row_plan_length(int M);
+// Rows per CTA and interleaved complex lines of a last-axis pass; rows32 is the
+// plan's tuned row count of the FP32 2-D operator (0 = size rule).
+void row_lines(int mode, int nfields, int ncomp, int M, int rows32, int* rows_per_cta, int* NL);
 
 // Field-level kernels (half-spectrum fields of one context).
 struct FieldGeom {

@@ -62,8 +62,9 @@ ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_p
 template <typename T>
 ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   using C = typename CT<T>::type;
-  if (sizeof(T) == 4 && pl.perm_ct != nullptr && ct_size(pl.M)) return launch_col_ct(sign, mode, a, pl, s);
-  const int TW = col_tile_width(pl.M, sizeof(C));
+  if (sizeof(T) == 4 && pl.ct_col && pl.perm_ct != nullptr && ct_size(pl.M)) return launch_col_ct(sign, mode, a, pl, s);
+  const int tuned = pl.tile[sizeof(T) == 4 ? 1 : 0];
+  const int TW = tuned > 0 ? tuned : col_tile_width(pl.M, sizeof(C));
   if (col_smem_bytes(pl.M, TW, sizeof(C)) > 220 * 1024) {
     set_error("transform length too large for one CTA: M=" + std::to_string(pl.M));
     return GHB_ERR_INVALID;
@@ -84,18 +85,13 @@ template ghb_status launch_col<double>(int, int, const ColArgs&, const FftPlan&,
 template ghb_status launch_col<float>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 
 // Rows a CTA transforms together in the operator's last-axis pass (d = 2:
-// 1 or 2; odd line counts always pair two rows).  0 = by size: two rows for
-// M <= 2048 (measured 29 % faster at M = 510), one row above.
-static int g_matvec_rows = 0;
-void set_matvec_rows(int r) { g_matvec_rows = (r == 1 || r == 2) ? r : 0; }
-static int g_row_M = 0;   // transform length of the pass being planned
-void set_row_plan_length(int M) { g_row_M = M; }
-
-void row_lines(int mode, int nfields, int ncomp, int* rows_per_cta, int* NL) {
+// 1 or 2, the tuned value or by size: two rows for M <= 2048, one above; odd
+// line counts always pair two rows).
+void row_lines(int mode, int nfields, int ncomp, int M, int rows32, int* rows_per_cta, int* NL) {
   const int per_row = nfields * ncomp;
   int r = 1;
   if (mode == ROW_MATVEC || mode == ROW_TOREAL) r = (per_row % 2 == 1) ? 2 : 1;
-  if (mode == ROW_MATVEC && per_row == 2) r = g_matvec_rows ? g_matvec_rows : (g_row_M <= 2048 ? 2 : 1);
+  if (mode == ROW_MATVEC && per_row == 2) r = (rows32 == 1 || rows32 == 2) ? rows32 : (M <= 2048 ? 2 : 1);
   *rows_per_cta = r;
   *NL = (r * per_row + 1) / 2;
 }
@@ -146,10 +142,10 @@ template ghb_status launch_row_batch<float>(int, int, const RowItem*, int, int64
 template <typename T>
 ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_t s) {
   int rows_per_cta = 1, NL = 1;
-  g_row_M = pl.M;
-  row_lines(mode, a.nfields, a.ncomp, &rows_per_cta, &NL);
+  row_lines(mode, a.nfields, a.ncomp, pl.M, sizeof(T) == 4 ? pl.rows32 : 0, &rows_per_cta, &NL);
   if (mode == ROW_MATVEC) {
-    if (sizeof(T) == 4 && pl.perm_ct != nullptr && ct_size(pl.M)) return launch_row_ct(NL, a, pl, rows_per_cta, s);
+    if (sizeof(T) == 4 && pl.ct_row && pl.perm_ct != nullptr && ct_size(pl.M))
+      return launch_row_ct(NL, a, pl, rows_per_cta, s);
     switch (NL) {
       case 1: return launch_row_nl<T, 1, ROW_MATVEC>(a, pl, rows_per_cta, s);
       case 2: return launch_row_nl<T, 2, ROW_MATVEC>(a, pl, rows_per_cta, s);

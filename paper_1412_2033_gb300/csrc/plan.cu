@@ -36,8 +36,10 @@ const Shape kShapes[] = {
     {SH_4, {4, 0, 0}},     {SH_5, {5, 0, 0}},
 };
 
+}  // namespace
+
 // Group consecutive stages into passes: at each stage take the first (longest)
-// shape that matches the next radices.
+// shape that matches the next radices with radix product <= maxprod.
 void group_passes(FftPlan& p, int k, int maxprod) {
   int t = 0, np = 0;
   while (t < p.nst) {
@@ -77,8 +79,6 @@ void group_passes(FftPlan& p, int k, int maxprod) {
     p.pdiv[k][i] = make_fastdiv(1);
   }
 }
-
-}  // namespace
 
 bool factorizable(int M) {
   std::vector<int> r;
@@ -147,6 +147,12 @@ ghb_status build_plan_tables(int M, FftPlan& p, PlanTables& t) {
 }
 
 ghb_status make_plan(int M, PlanHolder& out) {
+  ghb_status st = make_plan_untuned(M, out);
+  if (st != GHB_OK) return st;
+  return apply_tune(M, out.plan);
+}
+
+ghb_status make_plan_untuned(int M, PlanHolder& out) {
   PlanTables t;
   ghb_status st = build_plan_tables(M, out.plan, t);
   if (st != GHB_OK) return st;
@@ -168,6 +174,7 @@ ghb_status make_plan(int M, PlanHolder& out) {
   }
   p.perm = out.d_perm;
   p.perm_ct = out.d_perm_ct;
+  p.ct_col = p.ct_row = (out.d_perm_ct != nullptr) ? 1 : 0;
   p.tw64 = out.d_tw64;
   p.tw32 = out.d_tw32;
   return GHB_OK;

@@ -29,7 +29,8 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_gram", "ghb_bounds", "ghb_table_elems", "ghb_grid_elems", "ghb_copy_table",
            "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
            "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
-           "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc"]
+           "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc",
+           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -122,6 +123,9 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_batch_destroy": (None, [P]),
         "ghb_gram_noalloc": (i32, [i32, ip, ip, P, i32, ctypes.POINTER(P), dp, P]),
         "ghb_profile_read": (i32, [P, i32, ctypes.POINTER(i64), dp, dp, dp]),
+        "ghb_tune_get": (i32, [i32, ip]),
+        "ghb_tune_set": (i32, [i32, ip]),
+        "ghb_tune_reset": (i32, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -343,6 +347,33 @@ def gram_noalloc(d, N, M, grid, fields, stream=None):
     _check(lib.ghb_gram_noalloc(int(d), Nc, Mc, ctypes.c_void_p(grid.data_ptr()), len(fields), ptrs, out, s))
     m = len(fields)
     return np.array(out[: m * m]).reshape(m, m)
+
+
+TUNE_FIELDS = ["cap32", "tile32", "rows32", "ct_col", "ct_row", "cap64", "tile64"]
+
+
+def tune_get(M):
+    """Launch configuration of the transform passes for length M (ghb_tune_get;
+    tunes M first if it has not been tuned in this process)."""
+    lib = load_library()
+    cfg = (ctypes.c_int * 7)()
+    _check(lib.ghb_tune_get(int(M), cfg))
+    return dict(zip(TUNE_FIELDS, list(cfg)))
+
+
+def tune_set(M, **cfg):
+    """Fix the configuration of length M (ghb_tune_set); fields not given keep
+    their current values."""
+    cur = tune_get(M)
+    cur.update({k: int(v) for k, v in cfg.items()})
+    arr = (ctypes.c_int * 7)(*[cur[k] for k in TUNE_FIELDS])
+    _check(load_library().ghb_tune_set(int(M), arr))
+    return cur
+
+
+def tune_reset():
+    """Forget every stored configuration (ghb_tune_reset)."""
+    _check(load_library().ghb_tune_reset())
 
 
 class Batch:

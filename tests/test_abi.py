@@ -82,3 +82,27 @@ def test_null_arguments(lib):
     assert lib.ghb_matvec(None, 0, 0, 1, None, None, None) == 1
     assert lib.ghb_bounds(None, None, None, None) == 1
     lib.ghb_destroy(None)
+
+
+def test_tune_set_validation_and_size_rules(lib, monkeypatch):
+    """Launch configurations: ghb_tune_set validates before storing, and with
+    GHB_AUTOTUNE=0 ghb_tune_get answers with the size rules (no GPU work)."""
+    import paper_1412_2033_gb300 as g
+    monkeypatch.setenv("GHB_AUTOTUNE", "0")
+    g.tune_reset()
+    try:
+        assert g.tune_get(4374) == dict(cap32=32, tile32=0, rows32=0, ct_col=1, ct_row=1, cap64=18, tile64=0)
+        assert g.tune_get(510)["ct_col"] == 0                      # no specialised kernels at 510
+        bad = [dict(cap32=4), dict(cap32=33), dict(tile32=3), dict(tile64=16), dict(rows32=3),
+               dict(ct_col=2)]
+        for b in bad:
+            with pytest.raises(g.GhbError):
+                g.tune_set(4374, **b)
+        with pytest.raises(g.GhbError):
+            g.tune_set(510, ct_row=1)                               # only for lengths that have them
+        with pytest.raises(g.GhbError):
+            g.tune_get(4373)                                        # prime > 31
+        cfg = g.tune_set(510, cap32=18, tile32=4, rows32=1)
+        assert g.tune_get(510) == cfg
+    finally:
+        g.tune_reset()
