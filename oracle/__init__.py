@@ -16,6 +16,10 @@ arXiv:1412.2033):
                        (Remark anal_Fourier, eq. char_func_Four), the sphere
                        coefficient the paper does not print, and the
                        inclusion-matrix composite table (eq. inclcomp_formula).
+* ``gani``          -- the GaNi scheme (Def. GaNi, Algorithm 1): point samples
+                       of the coefficient, the trapezoidal-rule operator, the
+                       GaNi matrices and the a-posteriori guaranteed bounds
+                       (eq. GaNi_apost).
 * ``galerkin``      -- Helmholtz projections (Def. projection), the fully
                        populated Galerkin matrix (Lemma FD_matrix_full), the
                        double-grid values A_M (Lemma integ_eval_VM, eq. MBA_GA),
