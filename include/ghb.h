@@ -69,7 +69,12 @@ typedef enum {
 } ghb_status;
 
 typedef enum { GHB_BOX = 0, GHB_DISK = 1, GHB_SPHERE = 2 } ghb_shape;
-typedef enum { GHB_PRIMAL = 0, GHB_DUAL = 1 } ghb_kind;
+typedef enum {
+  GHB_PRIMAL = 0,       /* Ga operator, coefficient a (eq. GA_prim) */
+  GHB_DUAL = 1,         /* Ga operator, coefficient 1/a */
+  GHB_GANI_PRIMAL = 2,  /* ghb_matvec only: GaNi operator (Algorithm 1), samples of a */
+  GHB_GANI_DUAL = 3     /* ghb_matvec only: GaNi operator, samples of 1/a */
+} ghb_kind;
 typedef enum {
   GHB_FP64 = 0,   /* every operator application in FP64 */
   GHB_MIXED = 1,  /* FP32 inner CG inside an FP64 residual-correction loop; the
@@ -143,7 +148,8 @@ ghb_status ghb_get_grid(const ghb_ctx* ctx, int* d_out, int* N_out, int* M_out,
                         int64_t* field_elems);
 int64_t ghb_field_elems(const ghb_ctx* ctx);
 
-/* y = G A^full x (kind = GHB_PRIMAL: G_E and a; GHB_DUAL: G_J and 1/a) for one
+/* y = G A^full x (kind = GHB_PRIMAL: G_E and a; GHB_DUAL: G_J and 1/a; the
+ * GaNi operator G a~_N of Algorithm 1 for GHB_GANI_PRIMAL / GHB_GANI_DUAL) for one
  * field in the half-spectrum layout; precision GHB_FP64 (double pairs) or
  * GHB_FP32 (float pairs).  x_dev, y_dev: device pointers, caller-owned, not
  * overlapping.  project = 0 skips G (returns A^full x, used for energies).
@@ -171,6 +177,24 @@ ghb_status ghb_gram(ghb_ctx* ctx, int kind, int m, const void* const* fields_dev
  * matrices; upper[d*d] = U, lower[d*d] = D^{-1} (row-major, symmetrised).
  * infos (may be NULL) receives 2d entries: primal e_1..e_d, dual e_1..e_d. */
 ghb_status ghb_bounds(ghb_ctx* ctx, double* upper, double* lower, ghb_solve_info* infos);
+
+/* GaNi scheme (Def. GaNi, Algorithm 1) and its a-posteriori guaranteed bounds
+ * (eq. GaNi_apost).  The minimisers e~_i (primal) and j~_i (dual) of the
+ * trapezoidal-rule energies (1/|N|) sum_k a(x^k) v(x^k).v(x^k), x^k = k/N (a
+ * point on an inclusion's boundary counts as inside), are found by CG with the
+ * context's precision on the N grid; then
+ *   upper[d*d]      = a(E_i + e~_i, E_j + e~_j), the exact energies on the
+ *                     double grid (a guaranteed upper bound),
+ *   lower[d*d]      = inverse of a^{-1}(J_i + j~_i, J_j + j~_j) (guaranteed lower),
+ *   a_gani[d*d]     = the GaNi matrix A~_N (trapezoidal energies; may be NULL),
+ *   b_gani_inv[d*d] = B~_N^{-1} (may be NULL; equals A~_N for odd N, Remark
+ *                     duality_gani);
+ * row-major, symmetrised.  Every transform length N_a must have prime factors
+ * <= 31 (else GHB_ERR_INVALID).  infos as for ghb_bounds (energy = exact).
+ * The Ga bounds of ghb_bounds lie inside [lower, upper] (Ga minimises the exact
+ * energy over the same space).  Synchronous. */
+ghb_status ghb_bounds_gani(ghb_ctx* ctx, double* upper, double* lower, double* a_gani, double* b_gani_inv,
+                           ghb_solve_info* infos);
 
 /* Device data for checks: the coefficient table a^ (kind primal) or (1/a)^
  * (dual) on Z_{2N-1} as a half spectrum (centred leading axes of length

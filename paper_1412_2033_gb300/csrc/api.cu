@@ -34,6 +34,17 @@ struct Work {
   C* T2 = nullptr;
 };
 
+// One Galerkin operator: the geometry of its transforms, a plan per axis and
+// its real multiplier on the transform grid.  `ga`: Algorithm 2 on the double
+// grid M with the exact values A_M (eq. MBA_GA).  `gani`: Algorithm 1, the
+// same passes on the N grid (M = N) with the point samples of a (Def. GaNi).
+struct OpView {
+  Geometry g{};
+  const FftPlan* plan[3] = {nullptr, nullptr, nullptr};
+  double* grid64[2] = {nullptr, nullptr};
+  float* grid32[2] = {nullptr, nullptr};
+};
+
 struct ghb_ctx {
   Geometry g{};
   ghb_options opt{};
@@ -66,6 +77,18 @@ struct ghb_ctx {
   double* d_gram = nullptr;
   double* h_gram = nullptr;    // pinned
   int64_t bytes = 0;
+
+  // operators: the Ga one, the GaNi one (built on first use) and the one the
+  // CG, operator and Gram routines act on
+  OpView ga, gani;
+  const OpView* op = nullptr;
+  bool gani_ready = false;
+  PlanHolder planN[3];
+  int planN_of_axis[3] = {0, 1, 2};
+  double* gridN64[2] = {nullptr, nullptr};
+  float* gridN32[2] = {nullptr, nullptr};
+  double a0 = 1.0;      // microstructure, for the GaNi samples
+  int n_incs = 0;
 
   // optional per-launch CUDA-event timing (ghb_profile)
   bool prof = false;
@@ -228,6 +251,9 @@ ghb_status validate_phases(int d, double a0, const ghb_phase* phases, int n) {
 // field (Remark eval_with_FFT).
 ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
   const Geometry& g = c->g;
+  c->a0 = a0;
+  c->n_incs = n;
+  c->gani_ready = false;   // the GaNi samples follow the new microstructure on next use
   if (n > c->incs_cap) {   // two lists: kind 0 (a) and kind 1 (1/a)
     if (c->d_incs) cudaFree(c->d_incs);
     c->d_incs = nullptr;
@@ -248,6 +274,7 @@ ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
       }
       const double v = kind == 0 ? phases[i].value : 1.0 / phases[i].value;
       in.dv = v - a0v;
+      in.v = v;
     }
     if (n > 0) {
       GHB_CUDA_TRY(cudaMemcpy(c->d_incs + kind * c->incs_cap, h.data(), sizeof(Incl) * n,
@@ -310,10 +337,11 @@ template <typename C>
 ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* T2, const CgState* st,
                            bool pupdate, const C* pold, C* pnew) {
   using T = decltype(C{}.x);
-  const Geometry& g = c->g;
+  const OpView& V = *c->op;
+  const Geometry& g = V.g;
   const int d = g.d;
-  const void* grid = (sizeof(T) == 8) ? static_cast<const void*>(c->grid64[kind])
-                                      : static_cast<const void*>(c->grid32[kind]);
+  const void* grid = (sizeof(T) == 8) ? static_cast<const void*>(V.grid64[kind])
+                                      : static_cast<const void*>(V.grid32[kind]);
   ColArgs a{};
   a.in = in;
   a.out = T1;
@@ -326,7 +354,7 @@ ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* 
   a.Lout = g.M[0];
   constexpr bool f32 = sizeof(T) == 4;
   PROF(c, pupdate ? PK_COL1_INV_PU : PK_COL1_INV, f32,
-       launch_col<T>(+1, pupdate ? COL_PUPDATE : COL_PLAIN, a, plan_of(c, 0), c->stream));
+       launch_col<T>(+1, pupdate ? COL_PUPDATE : COL_PLAIN, a, *V.plan[0], c->stream));
   C* last = T1;
   if (d == 3) {
     ColArgs b{};
@@ -337,7 +365,7 @@ ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* 
     b.inner = g.h;
     b.Lin = g.N[1];
     b.Lout = g.M[1];
-    PROF(c, PK_COL2_INV, f32, launch_col<T>(+1, COL_PLAIN, b, plan_of(c, 1), c->stream));
+    PROF(c, PK_COL2_INV, f32, launch_col<T>(+1, COL_PLAIN, b, *V.plan[1], c->stream));
     last = T2;
   }
   RowArgs r{};
@@ -349,7 +377,7 @@ ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* 
   r.comp_stride = g.rows * g.h;
   r.a = grid;
   r.st = st;
-  PROF(c, PK_ROW, f32, launch_row<T>(ROW_MATVEC, r, plan_of(c, d - 1), c->stream));
+  PROF(c, PK_ROW, f32, launch_row<T>(ROW_MATVEC, r, *V.plan[d - 1], c->stream));
   if (d == 3) {
     ColArgs b{};
     b.in = T2;
@@ -359,7 +387,7 @@ ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* 
     b.inner = g.h;
     b.Lin = g.M[1];
     b.Lout = g.N[1];
-    PROF(c, PK_COL2_FWD, f32, launch_col<T>(-1, COL_PLAIN, b, plan_of(c, 1), c->stream));
+    PROF(c, PK_COL2_FWD, f32, launch_col<T>(-1, COL_PLAIN, b, *V.plan[1], c->stream));
   }
   ColArgs f{};
   f.in = T1;
@@ -369,7 +397,7 @@ ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* 
   f.inner = g.P / g.N[0];
   f.Lin = g.M[0];
   f.Lout = g.N[0];
-  PROF(c, PK_COL1_FWD, f32, launch_col<T>(-1, COL_PLAIN, f, plan_of(c, 0), c->stream));
+  PROF(c, PK_COL1_FWD, f32, launch_col<T>(-1, COL_PLAIN, f, *V.plan[0], c->stream));
   return GHB_OK;
 }
 
@@ -444,8 +472,8 @@ ghb_status apply_op(ghb_ctx* c, int kind, const C* x, C* y, bool project) {
 
 // Gram matrix (1/|M|) sum_m A_M(x_m) v_i(x_m).v_j(x_m) of m FP64 fields
 // (Lemma integ_eval_VM): inverse passes of each field, then one Gram pass.
-ghb_status gram(ghb_ctx* c, int kind, int m, const double2* const* fields, double* out) {
-  const Geometry& g = c->g;
+ghb_status gram(ghb_ctx* c, const OpView& V, int kind, int m, const double2* const* fields, double* out) {
+  const Geometry& g = V.g;
   const int d = g.d;
   RowArgs r{};
   for (int f = 0; f < m; ++f) {
@@ -456,7 +484,7 @@ ghb_status gram(ghb_ctx* c, int kind, int m, const double2* const* fields, doubl
     a.inner = g.P / g.N[0];
     a.Lin = g.N[0];
     a.Lout = g.M[0];
-    PROF(c, PK_COL1_INV, false, launch_col<double>(+1, COL_PLAIN, a, plan_of(c, 0), c->stream));
+    PROF(c, PK_COL1_INV, false, launch_col<double>(+1, COL_PLAIN, a, *V.plan[0], c->stream));
     r.t[f] = c->gT1[f];
     if (d == 3) {
       ColArgs b{};
@@ -466,7 +494,7 @@ ghb_status gram(ghb_ctx* c, int kind, int m, const double2* const* fields, doubl
       b.inner = g.h;
       b.Lin = g.N[1];
       b.Lout = g.M[1];
-      PROF(c, PK_COL2_INV, false, launch_col<double>(+1, COL_PLAIN, b, plan_of(c, 1), c->stream));
+      PROF(c, PK_COL2_INV, false, launch_col<double>(+1, COL_PLAIN, b, *V.plan[1], c->stream));
       r.t[f] = c->gT2[f];
     }
   }
@@ -475,12 +503,12 @@ ghb_status gram(ghb_ctx* c, int kind, int m, const double2* const* fields, doubl
   r.rows = g.rows;
   r.H = g.h;
   r.comp_stride = g.rows * g.h;
-  r.a = c->grid64[kind];
+  r.a = V.grid64[kind];
   r.partials = c->partials;
   r.gram = c->d_gram;
   r.ticket = c->ticket;
   r.scale = 1.0 / static_cast<double>(g.grid);
-  PROF(c, PK_GRAM_ROW, false, launch_row<double>(ROW_ENERGY, r, plan_of(c, d - 1), c->stream));
+  PROF(c, PK_GRAM_ROW, false, launch_row<double>(ROW_ENERGY, r, *V.plan[d - 1], c->stream));
   GHB_CUDA_TRY(cudaMemcpyAsync(c->h_gram, c->d_gram, sizeof(double) * m * m, cudaMemcpyDeviceToHost,
                                c->stream));
   GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -494,7 +522,15 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
   const Geometry& g = c->g;
   const FieldGeom fg = fgeom(g);
   ghb_solve_info inf{};
-  PROF(c, PK_MISC, false, launch_rhs<double>(c->b64, c->tab[kind], g, E, kind, c->stream));
+  if (c->op == &c->gani) {
+    // b = -G (a~ E)^: the constant field E through the unprojected operator
+    GHB_CUDA_TRY(cudaMemsetAsync(c->b64, 0, sizeof(double2) * g.field, c->stream));
+    PROF(c, PK_MISC, false, launch_add_constant(c->y64, c->b64, fg, E, c->stream));
+    TRY(apply_op<double2>(c, kind, c->y64, c->b64, true));
+    PROF(c, PK_MISC, false, launch_scale(c->b64, -1.0, g.field, c->stream));
+  } else {
+    PROF(c, PK_MISC, false, launch_rhs<double>(c->b64, c->tab[kind], g, E, kind, c->stream));
+  }
   const double tol = c->opt.tol;
   const int maxiter = c->opt.max_iter;
   int iters = 0, done = RUNNING;
@@ -577,7 +613,10 @@ void free_ctx(ghb_ctx* c) {
     if (p) cudaFree(p);
   };
   for (auto& p : c->plan) free_plan(p);
+  for (auto& p : c->planN) free_plan(p);
   for (int k = 0; k < 2; ++k) {
+    F(c->gridN64[k]);
+    F(c->gridN32[k]);
     F(c->tab[k]);
     F(c->grid64[k]);
     F(c->grid32[k]);
@@ -665,7 +704,77 @@ ghb_status alloc_ctx(ghb_ctx* c) {
   GHB_CUDA_TRY(cudaMemset(c->ticket, 0, sizeof(unsigned int)));
   GHB_CUDA_TRY(cudaMallocHost(&c->h_st, sizeof(CgState)));
   GHB_CUDA_TRY(cudaMallocHost(&c->h_gram, sizeof(double) * 9));
+  c->ga.g = g;
+  for (int a = 0; a < d; ++a) c->ga.plan[a] = &c->plan[c->plan_of_axis[a]].plan;
+  for (int k = 0; k < 2; ++k) {
+    c->ga.grid64[k] = c->grid64[k];
+    c->ga.grid32[k] = c->grid32[k];
+  }
+  c->op = &c->ga;
   return GHB_OK;
+}
+
+// The GaNi operator (Algorithm 1): transforms of length N (M = N), plans and
+// the point samples of a and 1/a on the N grid; built on first use and
+// resampled after ghb_set_coeffs.
+ghb_status ensure_gani(ghb_ctx* c) {
+  const Geometry& g = c->g;
+  const int d = g.d;
+  if (c->gani.plan[0] == nullptr) {
+    for (int a = 0; a < d; ++a)
+      if (!factorizable(g.N[a])) {
+        set_error("the GaNi transforms have length N; N=" + std::to_string(g.N[a]) +
+                  " has a prime factor above 31");
+        return GHB_ERR_INVALID;
+      }
+    Geometry gn = g;
+    for (int a = 0; a < d; ++a) gn.M[a] = g.N[a];
+    gn.T1 = static_cast<int64_t>(d) * gn.M[0] * (g.P / g.N[0]);
+    gn.T2 = d == 3 ? static_cast<int64_t>(d) * gn.M[0] * gn.M[1] * g.h : 0;
+    gn.rows = d == 2 ? gn.M[0] : static_cast<int64_t>(gn.M[0]) * gn.M[1];
+    gn.grid = 1;
+    for (int a = 0; a < d; ++a) gn.grid *= gn.M[a];
+    for (int a = 0; a < d; ++a) {
+      int found = -1;
+      for (int b = 0; b < a; ++b)
+        if (g.N[b] == g.N[a]) found = c->planN_of_axis[b];
+      if (found >= 0) {
+        c->planN_of_axis[a] = found;
+      } else {
+        c->planN_of_axis[a] = a;
+        TRY(make_plan(g.N[a], c->planN[a]));
+      }
+    }
+    for (int k = 0; k < 2; ++k) {
+      TRY(dmalloc(c, &c->gridN64[k], gn.grid));
+      TRY(dmalloc(c, &c->gridN32[k], gn.grid));
+    }
+    c->gani.g = gn;
+    for (int a = 0; a < d; ++a) c->gani.plan[a] = &c->planN[c->planN_of_axis[a]].plan;
+    for (int k = 0; k < 2; ++k) {
+      c->gani.grid64[k] = c->gridN64[k];
+      c->gani.grid32[k] = c->gridN32[k];
+    }
+  }
+  if (!c->gani_ready) {
+    for (int kind = 0; kind < 2; ++kind)
+      PROF(c, PK_COEFF, false, launch_sample_values(c->gridN64[kind], c->gridN32[kind], c->gani.g,
+                                                    c->d_incs + kind * c->incs_cap, c->n_incs,
+                                                    kind == 0 ? c->a0 : 1.0 / c->a0, c->stream));
+    c->gani_ready = true;
+  }
+  return GHB_OK;
+}
+
+// Runs f with the GaNi operator active.
+template <typename F>
+ghb_status with_gani(ghb_ctx* c, F&& f) {
+  TRY(ensure_gani(c));
+  const OpView* saved = c->op;
+  c->op = &c->gani;
+  const ghb_status st = f();
+  c->op = saved;
+  return st;
 }
 
 // Inverse of a symmetric positive definite d x d matrix (d <= 3) by cofactors.
@@ -907,19 +1016,24 @@ ghb_status ghb_matvec(ghb_ctx* c, int kind, int precision, int project, const vo
   ABI_GUARD_BEGIN
   clear_error();
   if (!c || !x_dev || !y_dev) { set_error("null argument"); return GHB_ERR_INVALID; }
-  if (kind != GHB_PRIMAL && kind != GHB_DUAL) { set_error("kind must be GHB_PRIMAL or GHB_DUAL"); return GHB_ERR_INVALID; }
+  if (kind < GHB_PRIMAL || kind > GHB_GANI_DUAL) {
+    set_error("kind must be GHB_PRIMAL, GHB_DUAL, GHB_GANI_PRIMAL or GHB_GANI_DUAL");
+    return GHB_ERR_INVALID;
+  }
   if (x_dev == y_dev) { set_error("x and y must not overlap"); return GHB_ERR_INVALID; }
+  if (precision != GHB_FP64 && precision != GHB_FP32) {
+    set_error("precision must be GHB_FP64 or GHB_FP32");
+    return GHB_ERR_INVALID;
+  }
   cudaStream_t saved = c->stream;
   if (stream) c->stream = static_cast<cudaStream_t>(stream);
-  ghb_status s;
-  if (precision == GHB_FP64)
-    s = apply_op<double2>(c, kind, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), project != 0);
-  else if (precision == GHB_FP32)
-    s = apply_op<float2>(c, kind, static_cast<const float2*>(x_dev), static_cast<float2*>(y_dev), project != 0);
-  else {
-    set_error("precision must be GHB_FP64 or GHB_FP32");
-    s = GHB_ERR_INVALID;
-  }
+  const int k = kind & 1;
+  auto run = [&]() -> ghb_status {
+    if (precision == GHB_FP64)
+      return apply_op<double2>(c, k, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), project != 0);
+    return apply_op<float2>(c, k, static_cast<const float2*>(x_dev), static_cast<float2*>(y_dev), project != 0);
+  };
+  const ghb_status s = kind >= GHB_GANI_PRIMAL ? with_gani(c, run) : run();
   c->stream = saved;
   return s;
   ABI_GUARD_END
@@ -936,7 +1050,7 @@ static ghb_status solve_abi(ghb_ctx* c, int kind, const double* E, void* field_o
   TRY(solve(c, kind, E, c->sol[0], &inf));
   const double2* f0 = c->sol[0];
   double en = 0.0;
-  TRY(gram(c, kind, 1, &f0, &en));
+  TRY(gram(c, *c->op, kind, 1, &f0, &en));
   inf.energy = en;
   if (field_out_dev) {
     GHB_CUDA_TRY(cudaMemcpyAsync(field_out_dev, c->sol[0], sizeof(double2) * c->g.field,
@@ -967,7 +1081,7 @@ ghb_status ghb_gram(ghb_ctx* c, int kind, int m, const void* const* fields_dev, 
     if (!fields_dev[i]) { set_error("null field"); return GHB_ERR_INVALID; }
     f[i] = static_cast<const double2*>(fields_dev[i]);
   }
-  return gram(c, kind == GHB_DUAL ? 1 : 0, m, f, out);
+  return gram(c, c->ga, kind == GHB_DUAL ? 1 : 0, m, f, out);
   ABI_GUARD_END
 }
 
@@ -988,7 +1102,7 @@ ghb_status ghb_bounds(ghb_ctx* c, double* upper, double* lower, ghb_solve_info* 
       if (infos) infos[kind * d + i] = inf;
     }
     const double2* f[3] = {c->sol[0], c->sol[1], d == 3 ? c->sol[2] : nullptr};
-    TRY(gram(c, kind, d, f, G[kind]));
+    TRY(gram(c, c->ga, kind, d, f, G[kind]));
     if (infos)
       for (int i = 0; i < d; ++i) infos[kind * d + i].energy = G[kind][i * d + i];
   }
@@ -1003,6 +1117,58 @@ ghb_status ghb_bounds(ghb_ctx* c, double* upper, double* lower, ghb_solve_info* 
   }
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) lower[i * d + j] = 0.5 * (L[i * d + j] + L[j * d + i]);
+  if (worst != GHB_OK) set_error("a solve did not reach the tolerance (the bounds are still guaranteed)");
+  return worst;
+  ABI_GUARD_END
+}
+
+ghb_status ghb_bounds_gani(ghb_ctx* c, double* upper, double* lower, double* a_gani, double* b_gani_inv,
+                           ghb_solve_info* infos) {
+  ABI_GUARD_BEGIN
+  clear_error();
+  if (!c || !upper || !lower) { set_error("null argument"); return GHB_ERR_INVALID; }
+  const int d = c->g.d;
+  ghb_status worst = GHB_OK;
+  double Gx[2][9], Gn[2][9];
+  for (int kind = 0; kind < 2; ++kind) {
+    TRY(with_gani(c, [&]() -> ghb_status {
+      for (int i = 0; i < d; ++i) {
+        double E[3] = {0, 0, 0};
+        E[i] = 1.0;
+        ghb_solve_info inf{};
+        TRY(solve(c, kind, E, c->sol[i], &inf));
+        if (inf.status != GHB_OK && worst == GHB_OK) worst = static_cast<ghb_status>(inf.status);
+        if (infos) infos[kind * d + i] = inf;
+      }
+      return GHB_OK;
+    }));
+    const double2* f[3] = {c->sol[0], c->sol[1], d == 3 ? c->sol[2] : nullptr};
+    TRY(gram(c, c->ga, kind, d, f, Gx[kind]));     // exact energies (eq. GaNi_apost)
+    TRY(gram(c, c->gani, kind, d, f, Gn[kind]));   // trapezoidal energies (Def. GaNi)
+    if (infos)
+      for (int i = 0; i < d; ++i) infos[kind * d + i].energy = Gx[kind][i * d + i];
+  }
+  auto sym = [&](const double* X, double* Y) {
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) Y[i * d + j] = 0.5 * (X[i * d + j] + X[j * d + i]);
+  };
+  auto inv_sym = [&](const double* X, double* Y) -> bool {
+    double S[9], L[9];
+    sym(X, S);
+    if (!inverse_small(d, S, L)) return false;
+    sym(L, Y);
+    return true;
+  };
+  sym(Gx[0], upper);
+  if (!inv_sym(Gx[1], lower)) {
+    set_error("dual Gram matrix is not positive definite");
+    return GHB_ERR_BREAKDOWN;
+  }
+  if (a_gani) sym(Gn[0], a_gani);
+  if (b_gani_inv && !inv_sym(Gn[1], b_gani_inv)) {
+    set_error("dual GaNi matrix is not positive definite");
+    return GHB_ERR_BREAKDOWN;
+  }
   if (worst != GHB_OK) set_error("a solve did not reach the tolerance (the bounds are still guaranteed)");
   return worst;
   ABI_GUARD_END

@@ -12,7 +12,8 @@
 //   admit     pending requests while the device-memory budget allows
 //             (coefficient set-up, right-hand sides, inner CG start),
 //   iterate   K batched FP32 CG iterations over every solve in its inner phase
-//             (solves whose inner CG has ended return at once from each kernel),
+//             (solves whose inner CG has ended return at once from each kernel);
+//             one iteration's launches are captured as a CUDA graph and replayed,
 //   correct   batched FP64 correction of the solves whose inner CG ended:
 //             x64 = G(x64 + dx), r64 = b - G A x64; stop or restart the inner CG,
 //   retire    batched Gram energies of the instances whose solves all ended;
@@ -181,6 +182,9 @@ struct ghb_batch {
   std::vector<int> free_states;
   Arena arena;
   int64_t launches = 0;
+  // one inner CG iteration's launches of the current cycle, captured once and
+  // replayed; destroyed after the next stream synchronisation
+  cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
@@ -303,6 +307,7 @@ ghb_status setup_coeffs(ghb_batch* b, Inst* in, const Request& rq) {
       }
       const double v = kind == 0 ? rq.phases[i].value : 1.0 / rq.phases[i].value;
       ic.dv = v - a0v;
+      ic.v = v;
     }
   }
   // stream-ordered: the block was allocated on this stream (pageable source, staged before return)
@@ -574,6 +579,10 @@ ghb_status read_states(ghb_batch* b) {
                                b->stream));
   GHB_CUDA_TRY(cudaStreamSynchronize(b->stream));
   b->arena.reset();
+  if (b->graph) {   // its replays have completed
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
   return GHB_OK;
 }
 
@@ -725,8 +734,31 @@ ghb_status iterate(ghb_batch* b, int K) {
   TRYB(prep_cg<float>(b, CG_PROJECT_DOT, pd, L));
   TRYB(prep_cg<float>(b, CG_UPDATE, up, L));
   TRYB(b->arena.flush(b->stream));
-  for (int it = 0; it < K; ++it)
-    for (const Launch& l : L) TRYB(run_launch(b, l));
+  // The K iterations launch the same kernels on the same work items: capture
+  // one iteration as a CUDA graph and replay it K times.
+  if (b->graph) {
+    GHB_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  GHB_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+  ghb_status st = GHB_OK;
+  for (const Launch& l : L) {
+    st = run_launch(b, l);
+    if (st != GHB_OK) break;
+  }
+  const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+  if (st != GHB_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != GHB_OK) return st;
+    GHB_CUDA_TRY(ce);
+  }
+  const cudaError_t ci = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  GHB_CUDA_TRY(ci);
+  for (int it = 0; it < K; ++it) GHB_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+  b->launches += static_cast<int64_t>(K - 1) * static_cast<int64_t>(L.size());   // run_launch counted one
   return GHB_OK;
 }
 
@@ -1071,6 +1103,7 @@ ghb_status ghb_batch_stats(const ghb_batch* b, int64_t* bytes_in_use, int* activ
 void ghb_batch_destroy(ghb_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   for (Inst* in : b->active) {
     if (in->block) cudaFreeAsync(in->block, b->stream);
     delete in;

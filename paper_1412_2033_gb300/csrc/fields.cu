@@ -691,4 +691,78 @@ ghb_status launch_add_constant(double2* v, const double2* e, const FieldGeom& fg
   return GHB_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// GaNi data: point samples of the coefficient (eq. approx_bilin)
+// ---------------------------------------------------------------------------
+namespace {
+
+// x^k = k / N per axis; a point belongs to an inclusion when its periodic
+// offset from the centre is at most the radius (disk, sphere) or at most half
+// the side along every axis (box).  The arithmetic is written with explicit
+// roundings (no fused multiply-add) so that the membership decisions are those
+// of the same formula evaluated operation by operation in FP64.
+__global__ void sample_kernel(double* out64, float* out32, Geometry g, const Incl* __restrict__ incs, int n,
+                              double a0v) {
+  const int d = g.d;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < g.grid;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int k[3] = {0, 0, 0};
+    int64_t rem = idx;
+    for (int a = d - 1; a >= 0; --a) {
+      k[a] = static_cast<int>(rem % g.N[a]);
+      rem /= g.N[a];
+    }
+    double v = a0v;
+    for (int i = 0; i < n; ++i) {
+      const Incl in = incs[i];
+      double dist[3] = {0.0, 0.0, 0.0};
+      for (int a = 0; a < d; ++a) {
+        const double t = __dsub_rn(__ddiv_rn(static_cast<double>(k[a]), static_cast<double>(g.N[a])), in.c[a]);
+        dist[a] = __dsub_rn(t, rint(t));
+      }
+      bool inside;
+      if (in.shape == GHB_BOX) {
+        inside = true;
+        for (int a = 0; a < d; ++a) inside = inside && (fabs(dist[a]) <= 0.5 * in.s[a]);
+      } else {
+        double s = __dmul_rn(dist[0], dist[0]);
+        for (int a = 1; a < d; ++a) s = __dadd_rn(s, __dmul_rn(dist[a], dist[a]));
+        inside = s <= __dmul_rn(in.s[0], in.s[0]);
+      }
+      if (inside) v = in.v;
+    }
+    out64[idx] = v;
+    out32[idx] = static_cast<float>(v);
+  }
+}
+
+__global__ void scale_kernel(double2* v, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double2 z = v[i];
+    v[i] = make_double2(s * z.x, s * z.y);
+  }
+}
+
+unsigned elementwise_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return static_cast<unsigned>(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+}  // namespace
+
+ghb_status launch_sample_values(double* out64, float* out32, const Geometry& g, const Incl* incs, int n,
+                                double a0v, cudaStream_t s) {
+  sample_kernel<<<elementwise_blocks(g.grid), 256, 0, s>>>(out64, out32, g, incs, n, a0v);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+
+ghb_status launch_scale(double2* v, double sc, int64_t n, cudaStream_t s) {
+  scale_kernel<<<elementwise_blocks(n), 256, 0, s>>>(v, sc, n);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+
 }  // namespace ghb

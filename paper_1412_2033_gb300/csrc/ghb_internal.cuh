@@ -57,6 +57,7 @@ struct Incl {
   double c[3];
   double s[3];
   double dv;       // (inside value - matrix value) of the coefficient tabulated
+  double v;        // the inside value itself (point samples of the GaNi scheme)
 };
 
 // ---------------------------------------------------------------------------
@@ -238,6 +239,12 @@ int64_t cg_blocks(const FieldGeom& fg);
 template <typename T>
 ghb_status launch_cg_batch(int op, const CgItem* items, int n, int64_t blocks, cudaStream_t s);
 ghb_status launch_to_f32_real(float* dst, const double* src, int64_t n, cudaStream_t s);
+// Point samples a(x^k), x^k = k / N (k_a = 0..N_a-1, C-order), of a0 + inclusions
+// (the GaNi scheme's data, eq. approx_bilin): FP64 and an FP32 copy.
+ghb_status launch_sample_values(double* out64, float* out32, const Geometry& g, const Incl* incs, int n,
+                                double a0v, cudaStream_t s);
+// v *= s for n complex entries
+ghb_status launch_scale(double2* v, double s, int64_t n, cudaStream_t st);
 ghb_status launch_add_constant(double2* v, const double2* e, const FieldGeom& fg, const double* E,
                                cudaStream_t s);
 

@@ -17,7 +17,7 @@ from .build import LIB
 
 GHB_OK, GHB_ERR_INVALID, GHB_ERR_OOM, GHB_ERR_NOT_CONVERGED, GHB_ERR_BREAKDOWN, GHB_ERR_CUDA = range(6)
 GHB_BOX, GHB_DISK, GHB_SPHERE = 0, 1, 2
-GHB_PRIMAL, GHB_DUAL = 0, 1
+GHB_PRIMAL, GHB_DUAL, GHB_GANI_PRIMAL, GHB_GANI_DUAL = 0, 1, 2, 3
 GHB_FP64, GHB_MIXED, GHB_FP32 = 0, 1, 2
 
 STATUS_NAMES = {0: "GHB_OK", 1: "GHB_ERR_INVALID", 2: "GHB_ERR_OOM", 3: "GHB_ERR_NOT_CONVERGED",
@@ -30,7 +30,7 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
            "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
            "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc",
-           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset"]
+           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset", "ghb_bounds_gani"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -126,6 +126,7 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_tune_get": (i32, [i32, ip]),
         "ghb_tune_set": (i32, [i32, ip]),
         "ghb_tune_reset": (i32, []),
+        "ghb_bounds_gani": (i32, [P, dp, dp, dp, dp, ctypes.POINTER(GhbSolveInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -316,6 +317,19 @@ class Context:
         U = np.array(up[: d * d]).reshape(d, d)
         L = np.array(lo[: d * d]).reshape(d, d)
         return U, L, [infos[i].as_dict() for i in range(2 * d)], st
+
+    def bounds_gani(self):
+        """(upper, lower, A_gani, B_gani_inv, infos, status): the a-posteriori
+        guaranteed bounds of the GaNi scheme (exact energies of the GaNi
+        minimisers, eq. GaNi_apost) and the GaNi matrices (ghb_bounds_gani)."""
+        d = self.d
+        bufs = [(ctypes.c_double * 9)() for _ in range(4)]
+        infos = (GhbSolveInfo * 6)()
+        st = _lib.ghb_bounds_gani(self._h, *bufs, infos)
+        if st not in (GHB_OK, GHB_ERR_NOT_CONVERGED):
+            _check(st)
+        mats = [np.array(b[: d * d]).reshape(d, d) for b in bufs]
+        return (*mats, [infos[i].as_dict() for i in range(2 * d)], st)
 
     # -- data for checks --------------------------------------------------------
     def table(self, kind=GHB_PRIMAL):
