@@ -22,6 +22,8 @@ Operators written out (each is the plain definition from the cited passage):
 * matvec_sampled -- the same operator at chosen output frequencies, directly
                    from the definition y(l) = G(l) sum_k a^(l-k) x(k)
                    (O(|N|) per output; usable at any N).
+* prolong        -- the coarse-to-fine prolongation of Section 7.4 (zero
+                   coefficients at the new frequencies: the same polynomial).
 * cg             -- conjugate gradients (Remark CG; Saad's Algorithm 6.18) on
                    the range of the projection, x0 = 0, stop when
                    ||r_k||_2 / ||b||_2 <= tol (the 2-norm over Z_N coefficients,
@@ -154,6 +156,17 @@ def constant_field(E, N) -> np.ndarray:
     f = np.zeros((d,) + tuple(N), dtype=np.complex128)
     f[(slice(None),) + tuple((n - 1) // 2 for n in N)] = np.asarray(E, dtype=np.float64)
     return f
+
+
+def prolong(x: np.ndarray, N) -> np.ndarray:
+    """I_N o I_M^{-1} (Section 7.4): the coefficients on Z_N of the trigonometric
+    polynomial with coefficients x on a smaller odd grid, zero elsewhere."""
+    d = x.shape[0]
+    Nc = x.shape[1:]
+    out = np.zeros((d,) + tuple(N), dtype=np.complex128)
+    sl = tuple(slice((n - nc) // 2, (n - nc) // 2 + nc) for n, nc in zip(N, Nc))
+    out[(slice(None),) + sl] = x
+    return out
 
 
 def rhs(table: np.ndarray, N, E, kind: str) -> np.ndarray:
