@@ -166,6 +166,31 @@ ghb_status ghb_solve_primal(ghb_ctx* ctx, const double* E, void* field_out_dev,
 ghb_status ghb_solve_dual(ghb_ctx* ctx, const double* J, void* field_out_dev,
                           ghb_solve_info* info);
 
+/* One solve with an initial guess and bound tracking (Section 7.4, the
+ * evolution of the bounds during CG, and the coarse-to-fine start).
+ *   kind: GHB_PRIMAL or GHB_DUAL; E[d]: load; field_out_dev, info: as for
+ *     ghb_solve_primal (info->energy is the exact energy of the final field);
+ *   x0_dev: initial fluctuation e_0, FP64 half spectrum of this context's N,
+ *     admissible (in the range of the projection, e.g. a prolongated coarse
+ *     solution minus its load); NULL = 0, the start at the Voigt (Reuss) value;
+ *   energies (host, may be NULL), cap >= 1: the energy a(E + e_i, E + e_i)
+ *     (primal; a^{-1}(.,.) dual) along the iterates, an upper bound (primal) or
+ *     the inverse of a lower bound (dual) at every step.  FP64 precision: one
+ *     value per CG iterate from the CG scalars, J(e_i) = J(e_0) -
+ *     sum_{j<i} alpha_j <r_j, r_j>, with J(e_0) evaluated exactly; mixed: the
+ *     start and every FP64 correction, each an exact Gram evaluation.
+ *     *n_energies (may be NULL) receives the count (at most cap).
+ * Returns the solve's status (GHB_ERR_NOT_CONVERGED keeps the outputs). */
+ghb_status ghb_solve_ex(ghb_ctx* ctx, int kind, const double* E, const void* x0_dev, void* field_out_dev,
+                        ghb_solve_info* info, double* energies, int cap, int* n_energies);
+
+/* Prolongation I_Nf o I_Nc^{-1} (Section 7.4): writes to xf_dev (Z_Nf) the
+ * coefficients of the same trigonometric polynomial as xc_dev (Z_Nc), zero at
+ * the frequencies outside Z_Nc; no approximation is made.  d fields of FP64
+ * half spectra (layout above), orders odd with Nf_a >= Nc_a.  Synchronous on
+ * `stream` (NULL = legacy default stream). */
+ghb_status ghb_prolong(int d, const int* Nc, const void* xc_dev, const int* Nf, void* xf_dev, void* stream);
+
 /* The Gram matrix out[i*m + j] = a(v_i, v_j) (kind primal) or a^{-1}(v_i, v_j)
  * (dual) of m <= 3 FP64 fields v_i given as device pointers, evaluated exactly
  * on the double grid in FP64 (Lemma integ_eval_VM): (1/|M|) sum_m A_M(x_m)

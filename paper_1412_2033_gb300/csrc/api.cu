@@ -1,6 +1,7 @@
 // C ABI of the ghb library: context, coefficient set-up, operator, CG solves
 // (FP64 and mixed FP32/FP64), Gram energies and bounds.  See include/ghb.h.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -89,6 +90,8 @@ struct ghb_ctx {
   float* gridN32[2] = {nullptr, nullptr};
   double a0 = 1.0;      // microstructure, for the GaNi samples
   int n_incs = 0;
+  double* d_hist = nullptr;   // energy decrease along CG iterates (bound tracking)
+  int hist_cap = 0;
 
   // optional per-launch CUDA-event timing (ghb_profile)
   bool prof = false;
@@ -518,7 +521,33 @@ ghb_status gram(ghb_ctx* c, const OpView& V, int kind, int m, const double2* con
 
 // One solve: minimiser over E_N (primal) / J_N (dual) for load E; the
 // admissible field E + e (FP64) is left in `field_out` (device).
-ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_solve_info* info) {
+// Exact energy a(E + e, E + e) (or a^{-1}) of the admissible field E + e held in
+// `scratch` after the call (Gram on the double grid).
+ghb_status energy_of(ghb_ctx* c, int kind, const double* E, const double2* e, double2* scratch, double* out) {
+  PROF(c, PK_MISC, false, launch_add_constant(scratch, e, fgeom(c->g), E, c->stream));
+  const double2* f = scratch;
+  return gram(c, c->ga, kind, 1, &f, out);
+}
+
+// Sets (or clears, hist = nullptr) the bound-tracking buffer of the CG state.
+ghb_status set_history(ghb_ctx* c, double* hist, int cap) {
+  CgState h{};
+  h.hist = hist;
+  h.hist_cap = cap;
+  GHB_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(c->st) + offsetof(CgState, hist), &h.hist,
+                               sizeof(double*) + sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return GHB_OK;
+}
+
+// One solve: minimiser over E_N (primal) / J_N (dual) for load E; the
+// admissible field E + e (FP64) is left in `field_out` (device).  x0: initial
+// fluctuation (admissible, FP64; null = 0).  energies: if not null, receives the
+// energy of E + e along the iterates (bound tracking, Section 7.4): FP64, every
+// CG iterate, J(x_i) = J(x_0) - sum_{j<i} alpha_j <r_j, r_j>; mixed, the start
+// and every FP64 correction, each an exact Gram evaluation.
+ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_solve_info* info,
+                 const double2* x0 = nullptr, std::vector<double>* energies = nullptr) {
   const Geometry& g = c->g;
   const FieldGeom fg = fgeom(g);
   ghb_solve_info inf{};
@@ -535,11 +564,60 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
   const int maxiter = c->opt.max_iter;
   int iters = 0, done = RUNNING;
   double rr = 0, bb = 0;
+  double J0 = 0.0;
+  if (energies) {
+    energies->clear();
+    if (x0) {
+      TRY(energy_of(c, kind, E, x0, field_out, &J0));
+    } else {
+      GHB_CUDA_TRY(cudaMemsetAsync(c->w64.q, 0, sizeof(double2) * g.field, c->stream));
+      TRY(energy_of(c, kind, E, c->w64.q, field_out, &J0));
+    }
+  }
   if (c->opt.precision == GHB_FP64) {
-    TRY(cg_run<double2>(c, kind, c->b64, tol, maxiter, &iters, &done, &rr, &bb));
+    const double2* rhs = c->b64;
+    double tol_run = tol, bb_full = 0.0;
+    if (x0) {
+      // ||b||^2, then b' = b - G A x0 (x0 admissible); CG on the correction
+      GHB_CUDA_TRY(cudaMemsetAsync(c->w64.q, 0, sizeof(double2) * g.field, c->stream));
+      PROF(c, PK_RESIDUAL, false, launch_residual(c->y64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
+      TRY(read_state(c));
+      bb_full = c->h_st->rr;
+      TRY(apply_op<double2>(c, kind, x0, c->w64.q, true));
+      PROF(c, PK_RESIDUAL, false, launch_residual(c->y64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
+      TRY(read_state(c));
+      const double bbp = c->h_st->rr;
+      rhs = c->y64;
+      tol_run = bbp > 0 ? std::min(0.5, tol * std::sqrt(bb_full / bbp)) : tol;
+    }
+    if (energies) {
+      const int cap = std::min(maxiter + 1, 1 << 20);
+      if (c->hist_cap < cap) {
+        if (c->d_hist) cudaFree(c->d_hist);
+        c->d_hist = nullptr;
+        c->hist_cap = 0;
+        TRY(dmalloc(c, &c->d_hist, cap));
+        c->hist_cap = cap;
+      }
+      TRY(set_history(c, c->d_hist, c->hist_cap));
+    }
+    const ghb_status st = cg_run<double2>(c, kind, rhs, tol_run, maxiter, &iters, &done, &rr, &bb);
+    if (energies) TRY(set_history(c, nullptr, 0));
+    TRY(st);
+    if (x0) {
+      PROF(c, PK_MISC, false, launch_axpy(c->w64.x, x0, 1.0, g.field, c->stream));
+      bb = bb_full;
+    }
     inf.iters = iters;
-    inf.matvecs_fp64 = iters;
+    inf.matvecs_fp64 = iters + (x0 ? 1 : 0);
     inf.relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+    if (energies) {
+      const int n = std::min(iters + 1, c->hist_cap);
+      std::vector<double> h(n);
+      GHB_CUDA_TRY(cudaMemcpyAsync(h.data(), c->d_hist, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+      GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      for (int i = 0; i < n; ++i) energies->push_back(J0 - h[i]);
+    }
     // exact projection of the iterate (admissibility up to FP64 rounding)
     PROF(c, PK_PROJECT, false, launch_project<double>(c->w64.q, c->w64.x, fg, kind, c->stream));
     PROF(c, PK_MISC, false, launch_add_constant(field_out, c->w64.q, fg, E, c->stream));
@@ -547,17 +625,26 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
     // FP64 residual correction around FP32 CG solves.  x64 (= y64) holds the
     // projected iterate, w64.x its unprojected accumulation.
     double2* x64 = c->y64;
-    GHB_CUDA_TRY(cudaMemsetAsync(x64, 0, sizeof(double2) * g.field, c->stream));
-    GHB_CUDA_TRY(cudaMemsetAsync(c->w64.x, 0, sizeof(double2) * g.field, c->stream));
     double2* r64 = c->w64.r;
-    GHB_CUDA_TRY(cudaMemcpyAsync(r64, c->b64, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice,
-                                 c->stream));
     // ||b||^2 through the FP64 residual kernel with y = 0
     GHB_CUDA_TRY(cudaMemsetAsync(c->w64.q, 0, sizeof(double2) * g.field, c->stream));
     PROF(c, PK_RESIDUAL, false, launch_residual(r64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
     TRY(read_state(c));
     bb = c->h_st->rr;
     rr = bb;
+    if (x0) {
+      GHB_CUDA_TRY(cudaMemcpyAsync(x64, x0, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice, c->stream));
+      GHB_CUDA_TRY(cudaMemcpyAsync(c->w64.x, x0, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+      TRY(apply_op<double2>(c, kind, x64, c->w64.q, true));
+      PROF(c, PK_RESIDUAL, false, launch_residual(r64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
+      TRY(read_state(c));
+      rr = c->h_st->rr;
+    } else {
+      GHB_CUDA_TRY(cudaMemsetAsync(x64, 0, sizeof(double2) * g.field, c->stream));
+      GHB_CUDA_TRY(cudaMemsetAsync(c->w64.x, 0, sizeof(double2) * g.field, c->stream));
+    }
+    if (energies) energies->push_back(J0);
     int outer = 0;
     int total_inner = 0, mv32 = 0, mv64 = 0;
     done = CONVERGED;
@@ -595,6 +682,11 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
         done = BREAKDOWN;
         break;
       }
+      if (energies) {
+        double J = 0.0;
+        TRY(energy_of(c, kind, E, x64, field_out, &J));
+        energies->push_back(J);
+      }
     }
     inf.iters = total_inner;
     inf.outer_iters = outer;
@@ -623,6 +715,7 @@ void free_ctx(ghb_ctx* c) {
   }
   F(c->tabT1);
   F(c->tabT2);
+  F(c->d_hist);
   F(c->d_incs);
   for (auto* W : {&c->w64}) {
     F(W->x); F(W->r); F(W->p); F(W->q); F(W->w); F(W->T1); F(W->T2);
@@ -1120,6 +1213,69 @@ ghb_status ghb_bounds(ghb_ctx* c, double* upper, double* lower, ghb_solve_info* 
   if (worst != GHB_OK) set_error("a solve did not reach the tolerance (the bounds are still guaranteed)");
   return worst;
   ABI_GUARD_END
+}
+
+ghb_status ghb_solve_ex(ghb_ctx* c, int kind, const double* E, const void* x0_dev, void* field_out_dev,
+                        ghb_solve_info* info, double* energies, int cap, int* n_energies) {
+  ABI_GUARD_BEGIN
+  clear_error();
+  if (!c || !E) { set_error("null argument"); return GHB_ERR_INVALID; }
+  if (kind != GHB_PRIMAL && kind != GHB_DUAL) { set_error("kind must be GHB_PRIMAL or GHB_DUAL"); return GHB_ERR_INVALID; }
+  if (energies && cap < 1) { set_error("cap must be >= 1 when energies is given"); return GHB_ERR_INVALID; }
+  for (int a = 0; a < c->g.d; ++a)
+    if (!std::isfinite(E[a])) { set_error("load must be finite"); return GHB_ERR_INVALID; }
+  std::vector<double> hist;
+  ghb_solve_info inf{};
+  TRY(solve(c, kind, E, c->sol[0], &inf, static_cast<const double2*>(x0_dev), energies ? &hist : nullptr));
+  const double2* f0 = c->sol[0];
+  double en = 0.0;
+  TRY(gram(c, c->ga, kind, 1, &f0, &en));
+  inf.energy = en;
+  if (field_out_dev) {
+    GHB_CUDA_TRY(cudaMemcpyAsync(field_out_dev, c->sol[0], sizeof(double2) * c->g.field,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  if (energies) {
+    const int n = static_cast<int>(std::min<size_t>(hist.size(), static_cast<size_t>(cap)));
+    for (int i = 0; i < n; ++i) energies[i] = hist[i];
+    if (n_energies) *n_energies = n;
+  } else if (n_energies) {
+    *n_energies = 0;
+  }
+  if (info) *info = inf;
+  if (inf.status != GHB_OK) set_error("the solve did not reach the tolerance (the bound is still guaranteed)");
+  return static_cast<ghb_status>(inf.status);
+  ABI_GUARD_END
+}
+
+ghb_status ghb_prolong(int d, const int* Nc, const void* xc_dev, const int* Nf, void* xf_dev, void* stream) {
+  clear_error();
+  if ((d != 2 && d != 3) || !Nc || !Nf || !xc_dev || !xf_dev) {
+    set_error("ghb_prolong: d must be 2 or 3 and no pointer may be NULL");
+    return GHB_ERR_INVALID;
+  }
+  FieldGeom fc{d, {1, 1, 1}, 0, 0}, ff{d, {1, 1, 1}, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    if (Nc[a] < 1 || Nc[a] % 2 == 0 || Nf[a] < Nc[a] || Nf[a] % 2 == 0) {
+      set_error("ghb_prolong: orders must be odd with N_fine >= N_coarse in every direction");
+      return GHB_ERR_INVALID;
+    }
+    fc.N[a] = Nc[a];
+    ff.N[a] = Nf[a];
+  }
+  fc.h = (Nc[d - 1] + 1) / 2;
+  ff.h = (Nf[d - 1] + 1) / 2;
+  fc.P = fc.h;
+  ff.P = ff.h;
+  for (int a = 0; a < d - 1; ++a) {
+    fc.P *= Nc[a];
+    ff.P *= Nf[a];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TRY(launch_prolong(static_cast<double2*>(xf_dev), ff, static_cast<const double2*>(xc_dev), fc, s));
+  GHB_CUDA_TRY(cudaStreamSynchronize(s));
+  return GHB_OK;
 }
 
 ghb_status ghb_bounds_gani(ghb_ctx* c, double* upper, double* lower, double* a_gani, double* b_gani_inv,

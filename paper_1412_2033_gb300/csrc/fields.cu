@@ -337,6 +337,8 @@ __device__ void op_init(const CgItem& it, int64_t bid, int64_t nb) {
     st->iter = 0;
     st->maxiter = it.maxiter;
     st->done = (tot == 0.0) ? CONVERGED : RUNNING;
+    st->dec = 0.0;
+    if (st->hist != nullptr && st->hist_cap > 0) st->hist[0] = 0.0;
   }
 }
 
@@ -412,7 +414,9 @@ __device__ void op_update(const CgItem& it, int64_t bid, int64_t nb) {
     const double rr_old = st->rr;
     st->beta = tot / rr_old;
     st->rr = tot;
+    st->dec += st->alpha * rr_old;
     st->iter += 1;
+    if (st->hist != nullptr && st->iter < st->hist_cap) st->hist[st->iter] = st->dec;
     if (!isfinite(tot)) st->done = BREAKDOWN;
     else if (tot <= st->tol2) st->done = CONVERGED;
     else if (st->iter >= st->maxiter) st->done = MAXITER;
@@ -761,6 +765,59 @@ ghb_status launch_sample_values(double* out64, float* out32, const Geometry& g, 
 
 ghb_status launch_scale(double2* v, double sc, int64_t n, cudaStream_t s) {
   scale_kernel<<<elementwise_blocks(n), 256, 0, s>>>(v, sc, n);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// prolongation Z_Nc -> Z_Nf and y += a x
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void prolong_kernel(double2* xf, FieldGeom ff, const double2* __restrict__ xc, FieldGeom fc) {
+  const int d = ff.d;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < ff.P;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    // fine index (i_1 .. i_{d-1} centred, j on the half axis) -> coarse index
+    int64_t rem = e;
+    const int j = static_cast<int>(rem % ff.h);
+    rem /= ff.h;
+    bool in = j < fc.h;
+    int64_t ec = j;
+    int64_t stride = fc.h;
+    for (int a = d - 2; a >= 0; --a) {
+      const int i = static_cast<int>(rem % ff.N[a]);
+      rem /= ff.N[a];
+      const int k = i - (ff.N[a] - 1) / 2;             // frequency
+      const int ic = k + (fc.N[a] - 1) / 2;
+      in = in && ic >= 0 && ic < fc.N[a];
+      ec += static_cast<int64_t>(ic) * stride;
+      stride *= fc.N[a];
+    }
+    for (int c = 0; c < d; ++c) xf[c * ff.P + e] = in ? xc[c * fc.P + ec] : make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void axpy_kernel(double2* y, const double2* __restrict__ x, double a, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double2 u = x[i], v = y[i];
+    y[i] = make_double2(v.x + a * u.x, v.y + a * u.y);
+  }
+}
+
+}  // namespace
+
+ghb_status launch_prolong(double2* xf, const FieldGeom& ff, const double2* xc, const FieldGeom& fc,
+                          cudaStream_t s) {
+  prolong_kernel<<<elementwise_blocks(ff.P), 256, 0, s>>>(xf, ff, xc, fc);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+
+ghb_status launch_axpy(double2* y, const double2* x, double a, int64_t n, cudaStream_t s) {
+  axpy_kernel<<<elementwise_blocks(n), 256, 0, s>>>(y, x, a, n);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }

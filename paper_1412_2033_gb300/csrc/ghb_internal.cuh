@@ -44,6 +44,13 @@ struct CgState {
   int pad;
   unsigned int ticket;  // last-block counter of the running reduction
   unsigned int pad2;
+  // bound tracking (Section 7.4): dec = sum_{j<iter} alpha_j <r_j, r_j>, the
+  // decrease of the energy along the CG iterates, J(x_i) = J(x_0) - dec_i;
+  // written to hist[i] for i < hist_cap when hist is not null
+  double dec;
+  double* hist;
+  int hist_cap;
+  int pad3;
 };
 
 constexpr int kMaxPartials = 4096;
@@ -245,6 +252,12 @@ ghb_status launch_sample_values(double* out64, float* out32, const Geometry& g, 
                                 double a0v, cudaStream_t s);
 // v *= s for n complex entries
 ghb_status launch_scale(double2* v, double s, int64_t n, cudaStream_t st);
+// y += a x for n complex entries
+ghb_status launch_axpy(double2* y, const double2* x, double a, int64_t n, cudaStream_t st);
+// Prolongation of a half-spectrum field from Z_Nc to Z_Nf (Nf_a >= Nc_a, odd):
+// the same trigonometric polynomial, coefficients outside Z_Nc zero.
+ghb_status launch_prolong(double2* xf, const FieldGeom& ff, const double2* xc, const FieldGeom& fc,
+                          cudaStream_t s);
 ghb_status launch_add_constant(double2* v, const double2* e, const FieldGeom& fg, const double* E,
                                cudaStream_t s);
 

@@ -30,7 +30,7 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
            "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
            "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc",
-           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset", "ghb_bounds_gani"]
+           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset", "ghb_bounds_gani", "ghb_solve_ex", "ghb_prolong"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -127,6 +127,8 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_tune_set": (i32, [i32, ip]),
         "ghb_tune_reset": (i32, []),
         "ghb_bounds_gani": (i32, [P, dp, dp, dp, dp, ctypes.POINTER(GhbSolveInfo)]),
+        "ghb_solve_ex": (i32, [P, i32, dp, P, P, ctypes.POINTER(GhbSolveInfo), dp, i32, ip]),
+        "ghb_prolong": (i32, [i32, ip, P, ip, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -318,6 +320,27 @@ class Context:
         L = np.array(lo[: d * d]).reshape(d, d)
         return U, L, [infos[i].as_dict() for i in range(2 * d)], st
 
+    def solve_ex(self, E, kind=GHB_PRIMAL, x0=None, energies=False, max_energies=100000):
+        """One solve (ghb_solve_ex): returns (field, info, energies, status); field
+        is the admissible E + e as a complex128 CUDA tensor of the half-spectrum
+        shape; x0: initial fluctuation (complex128 CUDA tensor or None);
+        energies: the energy along the iterates (bound tracking) when True."""
+        import torch
+        d = self.d
+        Ec = (ctypes.c_double * 3)(*([float(v) for v in E] + [0.0] * (3 - len(E))))
+        out = torch.empty(self.field_shape, dtype=torch.complex128, device="cuda")
+        info = GhbSolveInfo()
+        buf = (ctypes.c_double * max_energies)() if energies else None
+        n = ctypes.c_int(0)
+        x0p = None if x0 is None else ctypes.c_void_p(x0.contiguous().data_ptr())
+        torch.cuda.synchronize()
+        st = _lib.ghb_solve_ex(self._h, int(kind), Ec, x0p, ctypes.c_void_p(out.data_ptr()), ctypes.byref(info),
+                               buf, int(max_energies) if energies else 0, ctypes.byref(n))
+        if st not in (GHB_OK, GHB_ERR_NOT_CONVERGED):
+            _check(st)
+        hist = np.array(buf[: n.value]) if energies else None
+        return out, info.as_dict(), hist, st
+
     def bounds_gani(self):
         """(upper, lower, A_gani, B_gani_inv, infos, status): the a-posteriori
         guaranteed bounds of the GaNi scheme (exact energies of the GaNi
@@ -361,6 +384,22 @@ def gram_noalloc(d, N, M, grid, fields, stream=None):
     _check(lib.ghb_gram_noalloc(int(d), Nc, Mc, ctypes.c_void_p(grid.data_ptr()), len(fields), ptrs, out, s))
     m = len(fields)
     return np.array(out[: m * m]).reshape(m, m)
+
+
+def prolong(x, N_fine):
+    """ghb_prolong: the half-spectrum field x (complex128 CUDA tensor of order
+    N_coarse) as a field of order N_fine, the same trigonometric polynomial."""
+    import torch
+    d = x.shape[0]
+    Nc = list(x.shape[1:-1]) + [2 * x.shape[-1] - 1]
+    Nf = [int(n) for n in N_fine]
+    out = torch.empty((d,) + tuple(Nf[:-1]) + ((Nf[-1] + 1) // 2,), dtype=torch.complex128, device=x.device)
+    lib = load_library()
+    a = (ctypes.c_int * 3)(*(Nc + [1] * (3 - d)))
+    b = (ctypes.c_int * 3)(*(Nf + [1] * (3 - d)))
+    torch.cuda.synchronize()
+    _check(lib.ghb_prolong(d, a, ctypes.c_void_p(x.contiguous().data_ptr()), b, ctypes.c_void_p(out.data_ptr()), None))
+    return out
 
 
 TUNE_FIELDS = ["cap32", "tile32", "rows32", "ct_col", "ct_row", "cap64", "tile64"]
