@@ -16,6 +16,9 @@ arXiv:1412.2033):
                        (Remark anal_Fourier, eq. char_func_Four), the sphere
                        coefficient the paper does not print, and the
                        inclusion-matrix composite table (eq. inclcomp_formula).
+* ``image``         -- grid-based (pixel / voxel image) composites (Lemma
+                       grid_compos, Remark eval_with_FFT): the coefficient table
+                       of a piecewise-constant image and its Ga bounds.
 * ``gani``          -- the GaNi scheme (Def. GaNi, Algorithm 1): point samples
                        of the coefficient, the trapezoidal-rule operator, the
                        GaNi matrices and the a-posteriori guaranteed bounds

@@ -182,13 +182,20 @@ def rhs(table: np.ndarray, N, E, kind: str) -> np.ndarray:
 class Operator:
     """G A^full on Z_N for one material (primal) or its inverse (dual)."""
 
-    def __init__(self, mat: Material, N, kind: str, M=None, method: str = "double_grid"):
-        validate(mat)
+    def __init__(self, mat: Material, N, kind: str, M=None, method: str = "double_grid", table=None):
+        """``table``: the coefficient table on Z_{2N-1} of this kind's coefficient
+        when the material is not an inclusion-matrix composite (then ``mat`` may
+        be None), e.g. ``image.image_table`` of a pixel image."""
         self.N = list(N)
         self.d = len(N)
         self.kind = kind
-        self.mat = mat if kind == PRIMAL else mat.inverse()
-        self.table = coeff_table(self.mat, self.N)
+        if table is None:
+            validate(mat)
+            self.mat = mat if kind == PRIMAL else mat.inverse()
+            self.table = coeff_table(self.mat, self.N)
+        else:
+            self.mat = None
+            self.table = np.asarray(table, dtype=np.complex128)
         self.M = list(M) if M is not None else default_M(self.N)
         self.method = method
         if method == "double_grid":
