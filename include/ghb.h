@@ -133,6 +133,22 @@ void ghb_default_options(ghb_options* opt);
 ghb_status ghb_create(ghb_ctx** out, int d, const int* N, double a0,
                       const ghb_phase* phases, int n_phases, const ghb_options* opt);
 
+/* Grid-based composite (Lemma grid_compos, Remark eval_with_FFT): a(x) is the
+ * piecewise-constant pixel (voxel) image with image[p] on the pixel of side
+ * 1/P_a centred at x = p / P (periodic), p_a = 0 .. P_a - 1, C-order, host
+ * memory, every value positive and finite; P_a in 1..8192 with prime factors
+ * <= 31 (any relation to N is allowed: the image's spectrum is truncated or
+ * periodically extended to Z_{2N-1}).  The tables are a^(m) = prod_a
+ * sinc(m_a / P_a) (1/|P|) sum_p image[p] w_P^{-m.p} and the same for 1/image
+ * (the inverse of a pixel image is the pixel image of the inverses); the
+ * double-grid values follow as for inclusions.  Every solve and bound call
+ * then applies to the image; ghb_bounds_gani is not available (GHB_ERR_INVALID).
+ * ghb_set_image replaces the coefficients of an existing context (any
+ * resolution P); ghb_set_coeffs switches back to inclusions. */
+ghb_status ghb_create_image(ghb_ctx** out, int d, const int* N, const int* P, const double* image,
+                            const ghb_options* opt);
+ghb_status ghb_set_image(ghb_ctx* ctx, const int* P, const double* image);
+
 /* Replace the microstructure (same d, N, M): rebuild a^, (1/a)^, A_M, B_M. */
 ghb_status ghb_set_coeffs(ghb_ctx* ctx, double a0, const ghb_phase* phases, int n_phases);
 

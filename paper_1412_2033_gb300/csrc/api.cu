@@ -90,6 +90,7 @@ struct ghb_ctx {
   float* gridN32[2] = {nullptr, nullptr};
   double a0 = 1.0;      // microstructure, for the GaNi samples
   int n_incs = 0;
+  bool is_image = false;      // coefficients from a pixel image (no GaNi samples)
   double* d_hist = nullptr;   // energy decrease along CG iterates (bound tracking)
   int hist_cap = 0;
 
@@ -252,38 +253,11 @@ ghb_status validate_phases(int d, double a0, const ghb_phase* phases, int n) {
 // a^ (kind 0, values a) or (1/a)^ (kind 1, values 1/a) on Z_{2N-1}, then the
 // double-grid values (eq. MBA_GA) by the same padded inverse transforms as a
 // field (Remark eval_with_FFT).
-ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
+// Double-grid values A_M (eq. MBA_GA) of the table c->tab[kind]: the inverse
+// transforms of the table zero-padded from Z_{2N-1} to the double grid, then
+// the FP32 copy of the inner CG.
+ghb_status grids_from_table(ghb_ctx* c, int kind) {
   const Geometry& g = c->g;
-  c->a0 = a0;
-  c->n_incs = n;
-  c->gani_ready = false;   // the GaNi samples follow the new microstructure on next use
-  if (n > c->incs_cap) {   // two lists: kind 0 (a) and kind 1 (1/a)
-    if (c->d_incs) cudaFree(c->d_incs);
-    c->d_incs = nullptr;
-    c->incs_cap = 0;
-    TRY(dmalloc(c, &c->d_incs, 2 * static_cast<int64_t>(n)));
-    c->incs_cap = n;
-  }
-  for (int kind = 0; kind < 2; ++kind) {
-    std::vector<Incl> h(n);
-    const double a0v = kind == 0 ? a0 : 1.0 / a0;
-    for (int i = 0; i < n; ++i) {
-      Incl& in = h[i];
-      in.shape = phases[i].shape;
-      in.pad = 0;
-      for (int a = 0; a < 3; ++a) {
-        in.c[a] = a < g.d ? phases[i].center[a] : 0.0;
-        in.s[a] = phases[i].size[a];
-      }
-      const double v = kind == 0 ? phases[i].value : 1.0 / phases[i].value;
-      in.dv = v - a0v;
-      in.v = v;
-    }
-    if (n > 0) {
-      GHB_CUDA_TRY(cudaMemcpy(c->d_incs + kind * c->incs_cap, h.data(), sizeof(Incl) * n,
-                              cudaMemcpyHostToDevice));
-    }
-    PROF(c, PK_COEFF, false, launch_coeff_table(c->tab[kind], g, c->d_incs + kind * c->incs_cap, n, a0v, c->stream));
     const int Nd = g.N[g.d - 1];
     if (g.d == 2) {
       ColArgs a{};
@@ -330,7 +304,104 @@ ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
       PROF(c, PK_COEFF, false, launch_row<double>(ROW_TOREAL, r, plan_of(c, 2), c->stream));
     }
     PROF(c, PK_COEFF, false, launch_to_f32_real(c->grid32[kind], c->grid64[kind], g.grid, c->stream));
+  return GHB_OK;
+}
+
+ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
+  const Geometry& g = c->g;
+  c->a0 = a0;
+  c->n_incs = n;
+  c->is_image = false;
+  c->gani_ready = false;   // the GaNi samples follow the new microstructure on next use
+  if (n > c->incs_cap) {   // two lists: kind 0 (a) and kind 1 (1/a)
+    if (c->d_incs) cudaFree(c->d_incs);
+    c->d_incs = nullptr;
+    c->incs_cap = 0;
+    TRY(dmalloc(c, &c->d_incs, 2 * static_cast<int64_t>(n)));
+    c->incs_cap = n;
   }
+  for (int kind = 0; kind < 2; ++kind) {
+    std::vector<Incl> h(n);
+    const double a0v = kind == 0 ? a0 : 1.0 / a0;
+    for (int i = 0; i < n; ++i) {
+      Incl& in = h[i];
+      in.shape = phases[i].shape;
+      in.pad = 0;
+      for (int a = 0; a < 3; ++a) {
+        in.c[a] = a < g.d ? phases[i].center[a] : 0.0;
+        in.s[a] = phases[i].size[a];
+      }
+      const double v = kind == 0 ? phases[i].value : 1.0 / phases[i].value;
+      in.dv = v - a0v;
+      in.v = v;
+    }
+    if (n > 0) {
+      GHB_CUDA_TRY(cudaMemcpy(c->d_incs + kind * c->incs_cap, h.data(), sizeof(Incl) * n,
+                              cudaMemcpyHostToDevice));
+    }
+    PROF(c, PK_COEFF, false, launch_coeff_table(c->tab[kind], g, c->d_incs + kind * c->incs_cap, n, a0v, c->stream));
+    TRY(grids_from_table(c, kind));
+  }
+  return GHB_OK;
+}
+
+// Coefficient tables of a piecewise-constant pixel image (Lemma grid_compos,
+// Remark eval_with_FFT): the normalised P-sized DFT of the image (kind 0) and
+// of its inverse (kind 1) through the column passes, one axis at a time, then
+// a^(m) = prod_a sinc(m_a / P_a) C^(m mod P) on Z_{2N-1}, then the grid values.
+ghb_status build_image(ghb_ctx* c, const int* P, const double* image) {
+  const Geometry& g = c->g;
+  const int d = g.d;
+  int64_t np = 1;
+  for (int a = 0; a < d; ++a) np *= P[a];
+  c->is_image = true;
+  c->gani_ready = false;
+  std::vector<double2> h(np);
+  struct Scratch {   // two image-sized buffers, released on every exit
+    double2* p[2] = {nullptr, nullptr};
+    ~Scratch() {
+      for (double2* q : p)
+        if (q) cudaFree(q);
+    }
+  } sc;
+  GHB_CUDA_TRY(cudaMalloc(&sc.p[0], sizeof(double2) * np));
+  GHB_CUDA_TRY(cudaMalloc(&sc.p[1], sizeof(double2) * np));
+  double2* A = sc.p[0];
+  double2* B = sc.p[1];
+  PlanHolder plans[3];
+  struct FreePlans {
+    PlanHolder* p;
+    ~FreePlans() {
+      for (int a = 0; a < 3; ++a) free_plan(p[a]);
+    }
+  } fp{plans};
+  for (int a = 0; a < d; ++a) TRY(make_plan_untuned(P[a], plans[a]));
+  int Pc[3] = {1, 1, 1};
+  for (int a = 0; a < d; ++a) Pc[a] = P[a];
+  for (int kind = 0; kind < 2; ++kind) {
+    for (int64_t i = 0; i < np; ++i) h[i] = make_double2(kind == 0 ? image[i] : 1.0 / image[i], 0.0);
+    GHB_CUDA_TRY(cudaMemcpyAsync(A, h.data(), sizeof(double2) * np, cudaMemcpyHostToDevice, c->stream));
+    double2* src = A;
+    double2* dst = B;
+    int64_t outer = 1;
+    for (int a = 0; a < d; ++a) {
+      int64_t inner = 1;
+      for (int b2 = a + 1; b2 < d; ++b2) inner *= P[b2];
+      ColArgs f{};
+      f.in = src;
+      f.out = dst;
+      f.outer = outer;
+      f.inner = inner;
+      f.Lin = P[a];
+      f.Lout = P[a];
+      PROF(c, PK_COEFF, false, launch_col<double>(-1, COL_PLAIN, f, plans[a].plan, c->stream));
+      std::swap(src, dst);
+      outer *= P[a];
+    }
+    PROF(c, PK_COEFF, false, launch_image_table(c->tab[kind], g, src, Pc, c->stream));
+    TRY(grids_from_table(c, kind));
+  }
+  GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));   // before the scratch is released
   return GHB_OK;
 }
 
@@ -813,6 +884,10 @@ ghb_status alloc_ctx(ghb_ctx* c) {
 ghb_status ensure_gani(ghb_ctx* c) {
   const Geometry& g = c->g;
   const int d = g.d;
+  if (c->is_image) {
+    set_error("the GaNi scheme is built for inclusion-matrix composites, not pixel images");
+    return GHB_ERR_INVALID;
+  }
   if (c->gani.plan[0] == nullptr) {
     for (int a = 0; a < d; ++a)
       if (!factorizable(g.N[a])) {
@@ -1068,6 +1143,58 @@ ghb_status ghb_set_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n_
   TRY(build_coeffs(c, a0, phases, n_phases));
   GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return GHB_OK;
+  ABI_GUARD_END
+}
+
+namespace {
+ghb_status check_image(int d, const int* P, const double* image) {
+  if (!P || !image) {
+    set_error("P and image must not be NULL");
+    return GHB_ERR_INVALID;
+  }
+  int64_t np = 1;
+  for (int a = 0; a < d; ++a) {
+    if (P[a] < 1 || P[a] > 8192 || !factorizable(P[a])) {
+      set_error("image resolution P must lie in 1..8192 with prime factors <= 31");
+      return GHB_ERR_INVALID;
+    }
+    np *= P[a];
+  }
+  for (int64_t i = 0; i < np; ++i)
+    if (!(image[i] > 0.0) || !std::isfinite(image[i])) {
+      set_error("image values must be positive and finite (eq. A)");
+      return GHB_ERR_INVALID;
+    }
+  return GHB_OK;
+}
+}  // namespace
+
+ghb_status ghb_create_image(ghb_ctx** out, int d, const int* N, const int* P, const double* image,
+                            const ghb_options* opt) {
+  ABI_GUARD_BEGIN
+  clear_error();
+  if (!out) { set_error("out is NULL"); return GHB_ERR_INVALID; }
+  *out = nullptr;
+  if (d != 2 && d != 3) { set_error("d must be 2 or 3"); return GHB_ERR_INVALID; }
+  TRY(check_image(d, P, image));
+  ghb_ctx* c = nullptr;
+  TRY(ghb_create(&c, d, N, 1.0, nullptr, 0, opt));
+  const ghb_status s = build_image(c, P, image);
+  if (s != GHB_OK) {
+    ghb_destroy(c);
+    return s;
+  }
+  *out = c;
+  return GHB_OK;
+  ABI_GUARD_END
+}
+
+ghb_status ghb_set_image(ghb_ctx* c, const int* P, const double* image) {
+  ABI_GUARD_BEGIN
+  clear_error();
+  if (!c) { set_error("ctx is NULL"); return GHB_ERR_INVALID; }
+  TRY(check_image(c->g.d, P, image));
+  return build_image(c, P, image);
   ABI_GUARD_END
 }
 

@@ -822,4 +822,52 @@ ghb_status launch_axpy(double2* y, const double2* x, double a, int64_t n, cudaSt
   return GHB_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// coefficient table of a pixel image (Lemma grid_compos)
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ double pixel_sinc(int m, int P) {   // sinc(m / P) = sin(pi m / P) / (pi m / P)
+  if (m == 0) return 1.0;
+  const double x = static_cast<double>(m) / static_cast<double>(P);
+  return sinpi(x) / (3.141592653589793238462643383279502884 * x);
+}
+
+__global__ void image_table_kernel(double2* tab, Geometry g, const double2* __restrict__ chat, int3 P3) {
+  const int d = g.d;
+  const int P[3] = {P3.x, P3.y, P3.z};
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < g.table;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    // half table: leading axes centred on Z_{2N_a - 1}, last axis m_d = 0 .. N_d - 1
+    int m[3] = {0, 0, 0};
+    int64_t rem = e;
+    m[d - 1] = static_cast<int>(rem % g.N[d - 1]);
+    rem /= g.N[d - 1];
+    for (int a = d - 2; a >= 0; --a) {
+      const int L = 2 * g.N[a] - 1;
+      m[a] = static_cast<int>(rem % L) - (g.N[a] - 1);
+      rem /= L;
+    }
+    int64_t idx = 0;
+    double f = 1.0;
+    for (int a = 0; a < d; ++a) {
+      int i = (m[a] + (P[a] - 1) / 2) % P[a];
+      if (i < 0) i += P[a];
+      idx = idx * P[a] + i;
+      f *= pixel_sinc(m[a], P[a]);
+    }
+    const double2 cv = chat[idx];
+    tab[e] = make_double2(f * cv.x, f * cv.y);
+  }
+}
+
+}  // namespace
+
+ghb_status launch_image_table(double2* tab, const Geometry& g, const double2* chat, const int* P, cudaStream_t s) {
+  image_table_kernel<<<elementwise_blocks(g.table), 256, 0, s>>>(tab, g, chat, make_int3(P[0], P[1], P[2]));
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+
 }  // namespace ghb

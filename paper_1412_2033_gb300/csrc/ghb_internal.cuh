@@ -250,6 +250,11 @@ ghb_status launch_to_f32_real(float* dst, const double* src, int64_t n, cudaStre
 // (the GaNi scheme's data, eq. approx_bilin): FP64 and an FP32 copy.
 ghb_status launch_sample_values(double* out64, float* out32, const Geometry& g, const Incl* incs, int n,
                                 double a0v, cudaStream_t s);
+// Table of a pixel image (Lemma grid_compos with the pixel characteristic
+// function): tab(m) = prod_a sinc(m_a / P_a) Chat((m_a + (P_a - 1)/2) mod P_a),
+// m in Z_{2N-1} (half table); Chat = the image's normalised DFT with frequency
+// i - (P_a - 1)/2 at index i (the forward column pass with Lout = P_a).
+ghb_status launch_image_table(double2* tab, const Geometry& g, const double2* chat, const int* P, cudaStream_t s);
 // v *= s for n complex entries
 ghb_status launch_scale(double2* v, double s, int64_t n, cudaStream_t st);
 // y += a x for n complex entries

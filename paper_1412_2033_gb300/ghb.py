@@ -30,7 +30,8 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_copy_grid_values", "ghb_device_bytes", "ghb_last_error", "ghb_destroy", "ghb_version",
            "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
            "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc",
-           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset", "ghb_bounds_gani", "ghb_solve_ex", "ghb_prolong"]
+           "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset", "ghb_bounds_gani", "ghb_solve_ex", "ghb_prolong",
+           "ghb_create_image", "ghb_set_image"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -129,6 +130,8 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_bounds_gani": (i32, [P, dp, dp, dp, dp, ctypes.POINTER(GhbSolveInfo)]),
         "ghb_solve_ex": (i32, [P, i32, dp, P, P, ctypes.POINTER(GhbSolveInfo), dp, i32, ip]),
         "ghb_prolong": (i32, [i32, ip, P, ip, P, P]),
+        "ghb_create_image": (i32, [ctypes.POINTER(P), i32, ip, ip, dp, ctypes.POINTER(GhbOptions)]),
+        "ghb_set_image": (i32, [P, ip, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -204,6 +207,22 @@ class Context:
     @classmethod
     def from_microstructure(cls, m: dict, **options):
         return cls(m["d"], m["N"], m["a0"], m["inclusions"], **options)
+
+    @classmethod
+    def from_image(cls, image, N, **options):
+        """A context whose coefficient is the piecewise-constant pixel image
+        `image` (numpy array of shape P, positive values; ghb_create_image)."""
+        img = np.ascontiguousarray(np.asarray(image, dtype=np.float64))
+        d = img.ndim
+        ctx = cls(d, N, 1.0, [], **options)
+        ctx.set_image(img)
+        return ctx
+
+    def set_image(self, image):
+        """Replace the coefficient by a pixel image (ghb_set_image)."""
+        img = np.ascontiguousarray(np.asarray(image, dtype=np.float64))
+        P = (ctypes.c_int * 3)(*(list(img.shape) + [1] * (3 - img.ndim)))
+        _check(_lib.ghb_set_image(self._h, P, img.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     # -- lifetime -----------------------------------------------------------
     def close(self):
