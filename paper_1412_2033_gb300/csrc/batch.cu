@@ -403,8 +403,11 @@ ghb_status prep_col(ghb_batch* b, int sign, int mode, std::vector<ColItem>& item
   using C = typename CT<T>::type;
   int Mmax = 1;
   for (int M : Ms) Mmax = std::max(Mmax, M);
-  const int tuned = b->plans.count(Mmax) ? b->plans[Mmax].h.plan.tile[sizeof(T) == 4 ? 1 : 0] : 0;
-  const int TW = tuned > 0 ? tuned : col_tile_width(Mmax, sizeof(C));
+  // Launch shapes of the batched passes follow the size rules: the
+  // autotuner's tile widths are timed on one operand and measured slower for
+  // launches over many items of mixed lengths.  The items' radix groupings
+  // (their plans) are the tuned ones.
+  const int TW = col_tile_width(Mmax, sizeof(C));
   int64_t blocks = 0;
   for (auto& it : items) {
     it.block_begin = blocks;
@@ -434,8 +437,7 @@ ghb_status prep_row(ghb_batch* b, int mode, std::vector<RowItem>& items, const s
   int Mmax = 1;
   for (int M : Ms) Mmax = std::max(Mmax, M);
   int rpc = 1, NL = 1;
-  const int rows32 = (sizeof(T) == 4 && b->plans.count(Mmax)) ? b->plans[Mmax].h.plan.rows32 : 0;
-  row_lines(mode, nfields, ncomp, Mmax, rows32, &rpc, &NL);
+  row_lines(mode, nfields, ncomp, Mmax, 0, &rpc, &NL);
   int64_t blocks = 0;
   for (auto& it : items) {
     it.rows_per_cta = rpc;

@@ -10,7 +10,7 @@
 //                 runtime-plan ones.
 // How: on the first plan for M in the process, a square 2-D operand with the
 // largest odd N that M serves is allocated and every candidate is timed with
-// CUDA events on a private stream (2 untimed + 3 timed launches; the inverse
+// CUDA events on a private stream (1 untimed + 2 timed launches; the inverse
 // and forward column passes and the last-axis pass separately); the fastest
 // runtime-plan grouping by the sum of the three, then the specialised kernels
 // where they beat it.  Results stay for the life of the process.
@@ -77,15 +77,15 @@ struct Timer {
     if (e1) cudaEventDestroy(e1);
     if (s) cudaStreamDestroy(s);
   }
-  // mean milliseconds of one launch of fn (2 untimed, 3 timed)
+  // mean milliseconds of one launch of fn (1 untimed, 2 timed)
   template <typename F>
   ghb_status time(F&& fn, float* ms) {
-    for (int i = 0; i < 2; ++i) {
+    {
       const ghb_status st = fn();
       if (st != GHB_OK) return st;
     }
     GHB_CUDA_TRY(cudaEventRecord(e0, s));
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 2; ++i) {
       const ghb_status st = fn();
       if (st != GHB_OK) return st;
     }
@@ -93,18 +93,38 @@ struct Timer {
     GHB_CUDA_TRY(cudaEventSynchronize(e1));
     float t = 0;
     GHB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-    *ms = t / 3;
+    *ms = t / 2;
     return GHB_OK;
   }
 };
 
-struct Buffers {
+// Scratch of the timing runs, kept for the process and grown when a larger
+// length comes (releasing it would synchronise the whole device, stalling
+// work that other streams have in flight).
+struct Scratch {
   void* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  ~Buffers() {
-    for (void* q : p)
-      if (q) cudaFree(q);
-  }
+  size_t bytes[6] = {0, 0, 0, 0, 0, 0};
+  int device = -1;
 };
+Scratch g_scratch;
+
+ghb_status scratch(int i, size_t bytes, void** out) {
+  int dev = 0;
+  GHB_CUDA_TRY(cudaGetDevice(&dev));
+  if (g_scratch.device != dev) {   // another device: start over (the old buffers stay with it)
+    g_scratch = Scratch{};
+    g_scratch.device = dev;
+  }
+  if (g_scratch.bytes[i] < bytes) {
+    if (g_scratch.p[i]) cudaFree(g_scratch.p[i]);
+    g_scratch.p[i] = nullptr;
+    g_scratch.bytes[i] = 0;
+    GHB_CUDA_TRY(cudaMalloc(&g_scratch.p[i], bytes));
+    g_scratch.bytes[i] = bytes;
+  }
+  *out = g_scratch.p[i];
+  return GHB_OK;
+}
 
 #define TUNE_TRY(x)                      \
   do {                                   \
@@ -122,22 +142,26 @@ ghb_status tune_length(int M, Tune* out) {
     return GHB_OK;
   }
   const int h = (N + 1) / 2;
-  PlanHolder ph;
-  TUNE_TRY(make_plan_untuned(M, ph));
-  struct Release {
-    PlanHolder& p;
-    ~Release() { free_plan(p); }
-  } release{ph};
+  // the plan's device tables stay for the process (see Scratch)
+  static std::map<std::pair<int, int>, PlanHolder> plans;
+  int dev = 0;
+  GHB_CUDA_TRY(cudaGetDevice(&dev));
+  auto key = std::make_pair(dev, M);
+  if (!plans.count(key)) {
+    PlanHolder fresh;
+    TUNE_TRY(make_plan_untuned(M, fresh));
+    plans[key] = fresh;
+  }
+  const PlanHolder& ph = plans[key];
   Timer tm;
   TUNE_TRY(tm.init());
-  Buffers b;
+  struct {
+    void* p[6];
+  } b;
   const size_t nx = 2ull * N * h, nt = 2ull * M * h, ng = static_cast<size_t>(M) * M;
-  GHB_CUDA_TRY(cudaMalloc(&b.p[0], nx * sizeof(float2)));
-  GHB_CUDA_TRY(cudaMalloc(&b.p[1], nt * sizeof(float2)));
-  GHB_CUDA_TRY(cudaMalloc(&b.p[2], ng * sizeof(float)));
-  GHB_CUDA_TRY(cudaMalloc(&b.p[3], nx * sizeof(double2)));
-  GHB_CUDA_TRY(cudaMalloc(&b.p[4], nt * sizeof(double2)));
-  GHB_CUDA_TRY(cudaMalloc(&b.p[5], ng * sizeof(double)));
+  const size_t sz[6] = {nx * sizeof(float2), nt * sizeof(float2), ng * sizeof(float),
+                        nx * sizeof(double2), nt * sizeof(double2), ng * sizeof(double)};
+  for (int i = 0; i < 6; ++i) TUNE_TRY(scratch(i, sz[i], &b.p[i]));
   GHB_CUDA_TRY(cudaMemsetAsync(b.p[0], 0, nx * sizeof(float2), tm.s));
   GHB_CUDA_TRY(cudaMemsetAsync(b.p[1], 0, nt * sizeof(float2), tm.s));
   GHB_CUDA_TRY(cudaMemsetAsync(b.p[2], 0, ng * sizeof(float), tm.s));

@@ -108,6 +108,30 @@ def random_sphere_instance(seed, N=None):
     return _micro(3, [N, N, N], 1.0, incs)
 
 
+def voxel_foam(P=99, seed=BASE_SEED + 7, porosity=0.6, count=60):
+    """A seeded two-phase voxel image of size P^3 standing in for the fly-ash
+    foam image (Section 7.5, not available): pores are random overlapping balls
+    (radius U(0.05, 0.15), centres uniform) until the pore fraction reaches
+    `porosity`; solid voxels carry 0.49 and pore voxels 0.029 (the foam's phase
+    values).  Voxel p is centred at p / P (periodic)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(P) / P
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    pore = np.zeros((P, P, P), dtype=bool)
+    for _ in range(count * 10):
+        if pore.mean() >= porosity:
+            break
+        c = rng.uniform(0.0, 1.0, 3)
+        r = rng.uniform(0.05, 0.15)
+        d2 = np.zeros_like(X)
+        for g, cc in zip((X, Y, Z), c):
+            t = g - cc
+            t = t - np.rint(t)
+            d2 = d2 + t * t
+        pore |= d2 <= r * r
+    return np.where(pore, 0.029, 0.49)
+
+
 def request_stream(rate=200.0, duration=60.0, seed=BASE_SEED, d3_share=0.5,
                    n2=(63, 1023), n3=(15, 129)):
     """Poisson arrivals (mean ``rate`` per second) of bound requests mixing
