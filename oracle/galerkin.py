@@ -19,6 +19,9 @@ Operators written out (each is the plain definition from the cited passage):
                    inverse DFT, multiply by A_M, forward DFT (with 1/|M|),
                    truncate to Z_N, project.  By Lemma integ_eval_VM this equals
                    G A^full for every M >= 2N-1.
+* reduced_matvec -- the same operator by Lemma reduce_grid (Algorithm 3): 2^d
+                   shifted N-size transforms with the double-grid values of
+                   M = 2N read at the points 2r - s.
 * matvec_sampled -- the same operator at chosen output frequencies, directly
                    from the definition y(l) = G(l) sum_k a^(l-k) x(k)
                    (O(|N|) per output; usable at any N).
@@ -99,6 +102,31 @@ def matvec_double_grid(x: np.ndarray, a_M: np.ndarray, kind: str) -> np.ndarray:
     w = u * a_M[None]                                             # pointwise A_M
     wh = fdft_nd(w, axes)                                         # forward DFT, 1/|M|
     y = truncate_wrapped_to_centred(wh, N, lead=1)                # keep Z_N
+    return project(y, kind) if kind is not None else y
+
+
+def reduced_matvec(x: np.ndarray, a_2N: np.ndarray, kind) -> np.ndarray:
+    """G A^full x by Lemma reduce_grid (Algorithm 3), for the double grid 2N:
+    A^full = 2^-d sum_{s in {0,1}^d} S*(s) F_N A_N(s) F_N^{-1} S(s) with
+    S(s) = diag(omega_{2N}^{-s.m}), m in Z_N, and A_N(s) the values of the 2N grid
+    at the points 2r - s, r in Z_N (wrapped: the values at x = r/N - s/(2N))."""
+    d = x.shape[0]
+    N = list(x.shape[1:])
+    axes = range(1, d + 1)
+    m = [centred_freqs(n) for n in N]
+    y = np.zeros_like(x, dtype=np.complex128)
+    for s in np.ndindex(*([2] * d)):
+        ph = np.ones(N, dtype=np.complex128)
+        for a in range(d):
+            shape = [1] * d
+            shape[a] = N[a]
+            ph = ph * np.exp(-1j * np.pi * s[a] * m[a] / N[a]).reshape(shape)   # omega_{2N}^{-s m}
+        u = idft_nd(pad_centred_to_wrapped(x * ph[None], N, lead=1), axes)       # values at r/N - s/(2N)
+        idx = np.ix_(*[(2 * np.arange(n) - sa) % (2 * n) for n, sa in zip(N, s)])
+        w = u * a_2N[idx][None]
+        wh = truncate_wrapped_to_centred(fdft_nd(w, axes), N, lead=1)
+        y = y + np.conj(ph)[None] * wh
+    y = y / 2 ** d
     return project(y, kind) if kind is not None else y
 
 
