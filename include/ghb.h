@@ -122,6 +122,16 @@ typedef struct {
   double energy;         /* a(E+e, E+e) (primal) or a^{-1}(J+j, J+j) (dual), FP64 */
 } ghb_solve_info;
 
+/* Form of the Ga operator (the same operator, Lemma reduce_grid):
+ *   GHB_FORM_DOUBLE_GRID  Algorithm 2: one transform of length M per axis and
+ *                         line (the default);
+ *   GHB_FORM_REDUCED      Algorithm 3: for every s in {0,1}^d the N-length
+ *                         transforms of the field shifted by S(s) =
+ *                         diag(omega_2N^{-s.m}), multiplied by the double-grid
+ *                         values at the points 2r - s; needs M = 2N on every
+ *                         axis; N-sized intermediates. */
+typedef enum { GHB_FORM_DOUBLE_GRID = 0, GHB_FORM_REDUCED = 1 } ghb_form;
+
 /* Default options (tol 1e-10, FP64, automatic M). */
 void ghb_default_options(ghb_options* opt);
 
@@ -151,6 +161,13 @@ ghb_status ghb_set_image(ghb_ctx* ctx, const int* P, const double* image);
 
 /* Replace the microstructure (same d, N, M): rebuild a^, (1/a)^, A_M, B_M. */
 ghb_status ghb_set_coeffs(ghb_ctx* ctx, double a0, const ghb_phase* phases, int n_phases);
+
+/* Select the form of the Ga operator used by ghb_matvec (Ga kinds), the solves
+ * and the bounds (the Gram energies are always evaluated on the double grid).
+ * GHB_ERR_INVALID if the form is unknown, or GHB_FORM_REDUCED with M != 2N or
+ * with an N that has a prime factor above 31.  The sub-grids of the reduced
+ * form follow later coefficient changes. */
+ghb_status ghb_set_form(ghb_ctx* ctx, int form);
 
 /* Replace the options of an existing context (M is fixed at creation and ignored). */
 ghb_status ghb_set_options(ghb_ctx* ctx, const ghb_options* opt);

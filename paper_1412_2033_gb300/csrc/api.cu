@@ -33,6 +33,8 @@ struct Work {
   C* w = nullptr;
   C* T1 = nullptr;
   C* T2 = nullptr;
+  C* s1 = nullptr;   // reduced operator: the shifted direction and one shift's image
+  C* s2 = nullptr;
 };
 
 // One Galerkin operator: the geometry of its transforms, a plan per axis and
@@ -91,6 +93,13 @@ struct ghb_ctx {
   double a0 = 1.0;      // microstructure, for the GaNi samples
   int n_incs = 0;
   bool is_image = false;      // coefficients from a pixel image (no GaNi samples)
+  // reduced form of the Ga operator (Lemma reduce_grid, Algorithm 3; needs M = 2N):
+  // one N-grid view per shift s in {0,1}^d with the double-grid values at 2r - s
+  int form = GHB_FORM_DOUBLE_GRID;
+  bool red_ready = false;
+  OpView red[8];
+  double* redgrid64[2] = {nullptr, nullptr};
+  float* redgrid32[2] = {nullptr, nullptr};
   double* d_hist = nullptr;   // energy decrease along CG iterates (bound tracking)
   int hist_cap = 0;
 
@@ -312,6 +321,7 @@ ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
   c->a0 = a0;
   c->n_incs = n;
   c->is_image = false;
+  c->red_ready = false;
   c->gani_ready = false;   // the GaNi samples follow the new microstructure on next use
   if (n > c->incs_cap) {   // two lists: kind 0 (a) and kind 1 (1/a)
     if (c->d_incs) cudaFree(c->d_incs);
@@ -355,6 +365,7 @@ ghb_status build_image(ghb_ctx* c, const int* P, const double* image) {
   int64_t np = 1;
   for (int a = 0; a < d; ++a) np *= P[a];
   c->is_image = true;
+  c->red_ready = false;
   c->gani_ready = false;
   std::vector<double2> h(np);
   struct Scratch {   // two image-sized buffers, released on every exit
@@ -405,11 +416,12 @@ ghb_status build_image(ghb_ctx* c, const int* P, const double* image) {
   return GHB_OK;
 }
 
-// The passes of one operator application A^full x -> w (not yet projected),
-// reading x from `in` (column pass may also form p = r + beta p_old).
+// The passes of one operator application A^full x -> w (not yet projected)
+// through the active view c->op, reading x from `in` (the first column pass
+// may also form p = r + beta p_old).
 template <typename C>
-ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* T2, const CgState* st,
-                           bool pupdate, const C* pold, C* pnew) {
+ghb_status operator_passes_view(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* T2, const CgState* st,
+                                bool pupdate, const C* pold, C* pnew) {
   using T = decltype(C{}.x);
   const OpView& V = *c->op;
   const Geometry& g = V.g;
@@ -481,6 +493,42 @@ template <>
 Work<double2>& work<double2>(ghb_ctx* c) { return c->w64; }
 template <>
 Work<float2>& work<float2>(ghb_ctx* c) { return c->w32; }
+
+ghb_status ensure_reduced(ghb_ctx* c);
+
+// One operator application A^full x -> w: the active view's passes, or for the
+// Ga operator in its reduced form (Lemma reduce_grid, Algorithm 3)
+//   w = 2^-d sum_s S*(s) F_N [A_N(s) . F_N^-1 S(s) x],  S(s) = diag(omega_2N^{-s.m}),
+// each shift through the N-grid passes with the double-grid values at 2r - s
+// (the shift s = 0 carries the fused p update).
+template <typename C>
+ghb_status operator_passes(ghb_ctx* c, int kind, const C* in, C* out, C* T1, C* T2, const CgState* st,
+                           bool pupdate, const C* pold, C* pnew) {
+  if (c->op != &c->ga || c->form != GHB_FORM_REDUCED)
+    return operator_passes_view<C>(c, kind, in, out, T1, T2, st, pupdate, pold, pnew);
+  using T = decltype(C{}.x);
+  if (!c->red_ready) TRY(ensure_reduced(c));
+  Work<C>& W = work<C>(c);
+  const FieldGeom fg = fgeom(c->g);
+  const int ns = 1 << c->g.d;
+  const double sc = 1.0 / ns;
+  constexpr bool f32 = sizeof(T) == 4;
+  const OpView* saved = c->op;
+  c->op = &c->red[0];
+  ghb_status st0 = operator_passes_view<C>(c, kind, in, out, T1, T2, st, pupdate, pold, pnew);
+  const C* x = pupdate ? pnew : in;
+  for (int sh = 1; sh < ns && st0 == GHB_OK; ++sh) {
+    PROF(c, PK_MISC, f32, launch_phase<T>(W.s1, x, fg, sh, -1, 0.0, 1.0, st, c->stream));
+    c->op = &c->red[sh];
+    st0 = operator_passes_view<C>(c, kind, W.s1, W.s2, T1, T2, st, false, nullptr, nullptr);
+    if (st0 != GHB_OK) break;
+    const bool last = sh == ns - 1;
+    PROF(c, PK_MISC, f32, launch_phase<T>(out, W.s2, fg, sh, +1, last ? sc : 1.0, last ? sc : 1.0, st,
+                                          c->stream));
+  }
+  c->op = saved;
+  return st0;
+}
 
 // One CG iteration (Remark CG) on the work buffers of precision C; every
 // kernel returns at once when the device state says the solve is over.
@@ -778,6 +826,8 @@ void free_ctx(ghb_ctx* c) {
   for (auto& p : c->plan) free_plan(p);
   for (auto& p : c->planN) free_plan(p);
   for (int k = 0; k < 2; ++k) {
+    F(c->redgrid64[k]);
+    F(c->redgrid32[k]);
     F(c->gridN64[k]);
     F(c->gridN32[k]);
     F(c->tab[k]);
@@ -789,10 +839,10 @@ void free_ctx(ghb_ctx* c) {
   F(c->d_hist);
   F(c->d_incs);
   for (auto* W : {&c->w64}) {
-    F(W->x); F(W->r); F(W->p); F(W->q); F(W->w); F(W->T1); F(W->T2);
+    F(W->x); F(W->r); F(W->p); F(W->q); F(W->w); F(W->T1); F(W->T2); F(W->s1); F(W->s2);
   }
   for (auto* W : {&c->w32}) {
-    F(W->x); F(W->r); F(W->p); F(W->q); F(W->w); F(W->T1); F(W->T2);
+    F(W->x); F(W->r); F(W->p); F(W->q); F(W->w); F(W->T1); F(W->T2); F(W->s1); F(W->s2);
   }
   F(c->b64);
   F(c->y64);
@@ -878,6 +928,90 @@ ghb_status alloc_ctx(ghb_ctx* c) {
   return GHB_OK;
 }
 
+// Plans of length N_a (the N-grid operators: GaNi and the reduced Ga form).
+ghb_status ensure_planN(ghb_ctx* c) {
+  const Geometry& g = c->g;
+  const int d = g.d;
+  if (c->planN[c->planN_of_axis[0]].d_perm != nullptr) return GHB_OK;
+  for (int a = 0; a < d; ++a)
+    if (!factorizable(g.N[a])) {
+      set_error("the N-grid transforms have length N; N=" + std::to_string(g.N[a]) +
+                " has a prime factor above 31");
+      return GHB_ERR_INVALID;
+    }
+  for (int a = 0; a < d; ++a) {
+    int found = -1;
+    for (int b = 0; b < a; ++b)
+      if (g.N[b] == g.N[a]) found = c->planN_of_axis[b];
+    if (found >= 0) {
+      c->planN_of_axis[a] = found;
+    } else {
+      c->planN_of_axis[a] = a;
+      TRY(make_plan(g.N[a], c->planN[a]));
+    }
+  }
+  return GHB_OK;
+}
+
+// Geometry of the operators on the N grid (M = N).
+Geometry n_geometry(const Geometry& g) {
+  Geometry gn = g;
+  const int d = g.d;
+  for (int a = 0; a < d; ++a) gn.M[a] = g.N[a];
+  gn.T1 = static_cast<int64_t>(d) * gn.M[0] * (g.P / g.N[0]);
+  gn.T2 = d == 3 ? static_cast<int64_t>(d) * gn.M[0] * gn.M[1] * g.h : 0;
+  gn.rows = d == 2 ? gn.M[0] : static_cast<int64_t>(gn.M[0]) * gn.M[1];
+  gn.grid = 1;
+  for (int a = 0; a < d; ++a) gn.grid *= gn.M[a];
+  return gn;
+}
+
+// The reduced form (Lemma reduce_grid): for every shift s the N-grid view with
+// the double-grid values at 2r - s; needs M = 2N on every axis.  Built on first
+// use and refreshed after the coefficients change.
+ghb_status ensure_reduced(ghb_ctx* c) {
+  const Geometry& g = c->g;
+  const int d = g.d;
+  const int ns = 1 << d;
+  if (c->red[0].plan[0] == nullptr) {
+    for (int a = 0; a < d; ++a)
+      if (g.M[a] != 2 * g.N[a]) {
+        set_error("the reduced form needs the double grid M = 2N on every axis (Lemma reduce_grid)");
+        return GHB_ERR_INVALID;
+      }
+    TRY(ensure_planN(c));
+    const Geometry gn = n_geometry(g);
+    for (int k = 0; k < 2; ++k) {
+      TRY(dmalloc(c, &c->redgrid64[k], gn.grid * ns));
+      TRY(dmalloc(c, &c->redgrid32[k], gn.grid * ns));
+    }
+    for (auto* W : {&c->w64}) {
+      TRY(dmalloc(c, &W->s1, g.field));
+      TRY(dmalloc(c, &W->s2, g.field));
+    }
+    for (auto* W : {&c->w32}) {
+      TRY(dmalloc(c, &W->s1, g.field));
+      TRY(dmalloc(c, &W->s2, g.field));
+    }
+    for (int sh = 0; sh < ns; ++sh) {
+      c->red[sh].g = gn;
+      for (int a = 0; a < d; ++a) c->red[sh].plan[a] = &c->planN[c->planN_of_axis[a]].plan;
+      for (int k = 0; k < 2; ++k) {
+        c->red[sh].grid64[k] = c->redgrid64[k] + sh * gn.grid;
+        c->red[sh].grid32[k] = c->redgrid32[k] + sh * gn.grid;
+      }
+    }
+  }
+  if (!c->red_ready) {
+    for (int k = 0; k < 2; ++k)
+      for (int sh = 0; sh < ns; ++sh)
+        PROF(c, PK_COEFF, false, launch_subgrid(c->red[sh].grid64[k], c->red[sh].grid32[k], c->grid64[k], g, sh,
+                                                c->stream));
+    c->red_ready = true;
+  }
+  return GHB_OK;
+}
+
 // The GaNi operator (Algorithm 1): transforms of length N (M = N), plans and
 // the point samples of a and 1/a on the N grid; built on first use and
 // resampled after ghb_set_coeffs.
@@ -889,30 +1023,8 @@ ghb_status ensure_gani(ghb_ctx* c) {
     return GHB_ERR_INVALID;
   }
   if (c->gani.plan[0] == nullptr) {
-    for (int a = 0; a < d; ++a)
-      if (!factorizable(g.N[a])) {
-        set_error("the GaNi transforms have length N; N=" + std::to_string(g.N[a]) +
-                  " has a prime factor above 31");
-        return GHB_ERR_INVALID;
-      }
-    Geometry gn = g;
-    for (int a = 0; a < d; ++a) gn.M[a] = g.N[a];
-    gn.T1 = static_cast<int64_t>(d) * gn.M[0] * (g.P / g.N[0]);
-    gn.T2 = d == 3 ? static_cast<int64_t>(d) * gn.M[0] * gn.M[1] * g.h : 0;
-    gn.rows = d == 2 ? gn.M[0] : static_cast<int64_t>(gn.M[0]) * gn.M[1];
-    gn.grid = 1;
-    for (int a = 0; a < d; ++a) gn.grid *= gn.M[a];
-    for (int a = 0; a < d; ++a) {
-      int found = -1;
-      for (int b = 0; b < a; ++b)
-        if (g.N[b] == g.N[a]) found = c->planN_of_axis[b];
-      if (found >= 0) {
-        c->planN_of_axis[a] = found;
-      } else {
-        c->planN_of_axis[a] = a;
-        TRY(make_plan(g.N[a], c->planN[a]));
-      }
-    }
+    TRY(ensure_planN(c));
+    const Geometry gn = n_geometry(g);
     for (int k = 0; k < 2; ++k) {
       TRY(dmalloc(c, &c->gridN64[k], gn.grid));
       TRY(dmalloc(c, &c->gridN32[k], gn.grid));
@@ -1195,6 +1307,23 @@ ghb_status ghb_set_image(ghb_ctx* c, const int* P, const double* image) {
   if (!c) { set_error("ctx is NULL"); return GHB_ERR_INVALID; }
   TRY(check_image(c->g.d, P, image));
   return build_image(c, P, image);
+  ABI_GUARD_END
+}
+
+ghb_status ghb_set_form(ghb_ctx* c, int form) {
+  ABI_GUARD_BEGIN
+  clear_error();
+  if (!c) { set_error("ctx is NULL"); return GHB_ERR_INVALID; }
+  if (form != GHB_FORM_DOUBLE_GRID && form != GHB_FORM_REDUCED) {
+    set_error("form must be GHB_FORM_DOUBLE_GRID or GHB_FORM_REDUCED");
+    return GHB_ERR_INVALID;
+  }
+  if (form == GHB_FORM_REDUCED) {
+    TRY(ensure_reduced(c));
+    GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  c->form = form;
+  return GHB_OK;
   ABI_GUARD_END
 }
 

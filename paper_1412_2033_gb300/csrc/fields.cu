@@ -870,4 +870,93 @@ ghb_status launch_image_table(double2* tab, const Geometry& g, const double2* ch
   return GHB_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// reduced Ga operator (Lemma reduce_grid): sub-grids and DFT shifts
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void subgrid_kernel(double* out64, float* out32, const double* __restrict__ grid, Geometry g,
+                               int shift, int64_t n) {
+  const int d = g.d;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t rem = e, idx = 0, stride = 1;
+    int r[3] = {0, 0, 0};
+    for (int a = d - 1; a >= 0; --a) {
+      r[a] = static_cast<int>(rem % g.N[a]);
+      rem /= g.N[a];
+    }
+    for (int a = d - 1; a >= 0; --a) {
+      const int sa = (shift >> a) & 1;
+      int m = 2 * r[a] - sa;
+      if (m < 0) m += g.M[a];
+      idx += static_cast<int64_t>(m) * stride;
+      stride *= g.M[a];
+    }
+    const double v = grid[idx];
+    out64[e] = v;
+    out32[e] = static_cast<float>(v);
+  }
+}
+
+template <typename T>
+__global__ void phase_kernel(typename CT<T>::type* y, const typename CT<T>::type* __restrict__ x, FieldGeom fg,
+                             int shift, int sign, T a, T b, const CgState* st) {
+  using C = typename CT<T>::type;
+  if (st != nullptr && st->done != RUNNING) return;
+  const int d = fg.d;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t rem = e;
+    const int j = static_cast<int>(rem % fg.h);
+    rem /= fg.h;
+    // sum_a s_a m_a / N_a, m the frequency (leading axes centred, last axis j)
+    T t = ((shift >> (d - 1)) & 1) ? static_cast<T>(j) / static_cast<T>(fg.N[d - 1]) : T(0);
+    for (int ax = d - 2; ax >= 0; --ax) {
+      const int i = static_cast<int>(rem % fg.N[ax]);
+      rem /= fg.N[ax];
+      if ((shift >> ax) & 1) t += static_cast<T>(i - (fg.N[ax] - 1) / 2) / static_cast<T>(fg.N[ax]);
+    }
+    T sn, cs;
+    if constexpr (sizeof(T) == 8) sincospi(static_cast<double>(sign) * t, &sn, &cs);
+    else sincospif(static_cast<float>(sign) * t, &sn, &cs);
+    for (int c = 0; c < d; ++c) {
+      const C xv = x[c * fg.P + e];
+      const C rot = mk(b * (cs * xv.x - sn * xv.y), b * (cs * xv.y + sn * xv.x));
+      if (a == T(0)) {
+        y[c * fg.P + e] = rot;
+      } else {
+        const C yv = y[c * fg.P + e];
+        y[c * fg.P + e] = mk(a * yv.x + rot.x, a * yv.y + rot.y);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+ghb_status launch_subgrid(double* out64, float* out32, const double* grid64, const Geometry& g, int shift,
+                          cudaStream_t s) {
+  int64_t n = 1;
+  for (int a = 0; a < g.d; ++a) n *= g.N[a];
+  subgrid_kernel<<<elementwise_blocks(n), 256, 0, s>>>(out64, out32, grid64, g, shift, n);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+
+template <typename T>
+ghb_status launch_phase(void* y, const void* x, const FieldGeom& fg, int shift, int sign, double a, double b,
+                        const CgState* st, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  phase_kernel<T><<<elementwise_blocks(fg.P), 256, 0, s>>>(static_cast<C*>(y), static_cast<const C*>(x), fg, shift,
+                                                           sign, static_cast<T>(a), static_cast<T>(b), st);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
+template ghb_status launch_phase<double>(void*, const void*, const FieldGeom&, int, int, double, double,
+                                         const CgState*, cudaStream_t);
+template ghb_status launch_phase<float>(void*, const void*, const FieldGeom&, int, int, double, double,
+                                        const CgState*, cudaStream_t);
+
 }  // namespace ghb

@@ -255,6 +255,16 @@ ghb_status launch_sample_values(double* out64, float* out32, const Geometry& g, 
 // m in Z_{2N-1} (half table); Chat = the image's normalised DFT with frequency
 // i - (P_a - 1)/2 at index i (the forward column pass with Lout = P_a).
 ghb_status launch_image_table(double2* tab, const Geometry& g, const double2* chat, const int* P, cudaStream_t s);
+// Reduced Ga operator (Lemma reduce_grid): the values of the 2N grid at the
+// points 2r - s (r in Z_N wrapped, s in {0,1}^d given by the bits of `shift`)
+// as an N grid, FP64 and FP32 (g: the context's geometry with M = 2N).
+ghb_status launch_subgrid(double* out64, float* out32, const double* grid64, const Geometry& g, int shift,
+                          cudaStream_t s);
+// y = a y + b exp(sign pi i s.m / N) x over a half-spectrum field (m the
+// frequency, s the bits of `shift`), skipped when st says the solve is over.
+template <typename T>
+ghb_status launch_phase(void* y, const void* x, const FieldGeom& fg, int shift, int sign, double a, double b,
+                        const CgState* st, cudaStream_t s);
 // v *= s for n complex entries
 ghb_status launch_scale(double2* v, double s, int64_t n, cudaStream_t st);
 // y += a x for n complex entries
@@ -284,8 +294,11 @@ __host__ __device__ constexpr int col_tile_width(int M, int elem_bytes) {
 }
 
 // Transform lengths with size-specialised FP32 operator kernels (fft_ct.cuh):
-// the double grids 2 * 3^k of the 2-D operator at N = 81, 243, 729, 2187.
-__host__ __device__ constexpr bool ct_size(int M) { return M == 162 || M == 486 || M == 1458 || M == 4374; }
+// the double grids 2 * 3^k of the 2-D operator at N = 81, 243, 729, 2187, and
+// 2187 itself (the reduced operator's transforms at N = 2187).
+__host__ __device__ constexpr bool ct_size(int M) {
+  return M == 162 || M == 486 || M == 1458 || M == 4374 || M == 2187;
+}
 ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
 ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
 

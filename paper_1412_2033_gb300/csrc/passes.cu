@@ -41,6 +41,7 @@ ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl
     case 486: return launch_col_ct_m<486>(sign, mode, a, pl, s);
     case 1458: return launch_col_ct_m<1458>(sign, mode, a, pl, s);
     case 4374: return launch_col_ct_m<4374>(sign, mode, a, pl, s);
+    case 2187: return launch_col_ct_m<2187>(sign, mode, a, pl, s);
     default: break;
   }
   set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
@@ -53,6 +54,7 @@ ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_p
     case 486: return launch_row_ct_m<486>(NL, a, pl, rows_per_cta, s);
     case 1458: return launch_row_ct_m<1458>(NL, a, pl, rows_per_cta, s);
     case 4374: return launch_row_ct_m<4374>(NL, a, pl, rows_per_cta, s);
+    case 2187: return launch_row_ct_m<2187>(NL, a, pl, rows_per_cta, s);
     default: break;
   }
   set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));

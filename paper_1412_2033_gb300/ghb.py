@@ -19,6 +19,7 @@ GHB_OK, GHB_ERR_INVALID, GHB_ERR_OOM, GHB_ERR_NOT_CONVERGED, GHB_ERR_BREAKDOWN, 
 GHB_BOX, GHB_DISK, GHB_SPHERE = 0, 1, 2
 GHB_PRIMAL, GHB_DUAL, GHB_GANI_PRIMAL, GHB_GANI_DUAL = 0, 1, 2, 3
 GHB_FP64, GHB_MIXED, GHB_FP32 = 0, 1, 2
+GHB_FORM_DOUBLE_GRID, GHB_FORM_REDUCED = 0, 1
 
 STATUS_NAMES = {0: "GHB_OK", 1: "GHB_ERR_INVALID", 2: "GHB_ERR_OOM", 3: "GHB_ERR_NOT_CONVERGED",
                 4: "GHB_ERR_BREAKDOWN", 5: "GHB_ERR_CUDA"}
@@ -31,7 +32,7 @@ EXPORTS = ["ghb_default_options", "ghb_create", "ghb_set_coeffs", "ghb_set_optio
            "ghb_profile", "ghb_profile_read", "ghb_batch_create", "ghb_batch_submit", "ghb_batch_step",
            "ghb_batch_run", "ghb_batch_results", "ghb_batch_stats", "ghb_batch_destroy", "ghb_gram_noalloc",
            "ghb_tune_get", "ghb_tune_set", "ghb_tune_reset", "ghb_bounds_gani", "ghb_solve_ex", "ghb_prolong",
-           "ghb_create_image", "ghb_set_image"]
+           "ghb_create_image", "ghb_set_image", "ghb_set_form"]
 
 PROFILE_CLASSES = ["coeff", "col1_inv_pupdate", "col1_inv", "col2_inv", "row_matvec", "col2_fwd", "col1_fwd",
                    "project_dot", "update", "project", "residual", "gram_row", "misc"]
@@ -132,6 +133,7 @@ def load_library(path: str = LIB) -> ctypes.CDLL:
         "ghb_prolong": (i32, [i32, ip, P, ip, P, P]),
         "ghb_create_image": (i32, [ctypes.POINTER(P), i32, ip, ip, dp, ctypes.POINTER(GhbOptions)]),
         "ghb_set_image": (i32, [P, ip, dp]),
+        "ghb_set_form": (i32, [P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -217,6 +219,11 @@ class Context:
         ctx = cls(d, N, 1.0, [], **options)
         ctx.set_image(img)
         return ctx
+
+    def set_form(self, form):
+        """"double_grid" (Algorithm 2) or "reduced" (Algorithm 3, needs M = 2N)."""
+        f = {"double_grid": GHB_FORM_DOUBLE_GRID, "reduced": GHB_FORM_REDUCED}[form]
+        _check(_lib.ghb_set_form(self._h, f))
 
     def set_image(self, image):
         """Replace the coefficient by a pixel image (ghb_set_image)."""
