@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the plain FP64 path (comparison)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reduced-steps", type=int, default=1,
+                    help="bound pairs timed with the reduced form of the operator (0 = skip)")
     ap.add_argument("--image-steps", type=int, default=1,
                     help="voxel-image bound pairs timed (0 = skip)")
     ap.add_argument("--image-N", type=int, default=99, help="order N of the voxel-image workload")
@@ -389,6 +391,28 @@ def run_ours(args, world, rank, local):
         cfine.close()
         ccoarse.close()
 
+    # ---- reduced form of the operator (Algorithm 3) on the same workload
+    reduced = None
+    if args.reduced_steps > 0 and all(mm == 2 * nn for mm, nn in zip(ctx.M, m["N"])):
+        cr = g.Context.from_microstructure(m, precision="mixed", tol=1e-10)
+        cr.set_stream(stream)
+        bytes_dg = cr.device_bytes()
+        cr.set_form("reduced")
+        cr.bounds()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.reduced_steps):
+            cr.set_coeffs(m["a0"], incs)
+            RU, RL, rinf, _ = cr.bounds()
+        torch.cuda.synchronize()
+        tr = (time.perf_counter() - t0) / args.reduced_steps
+        reduced = {"bound_pairs_per_s": 1.0 / tr, "s_per_pair": tr,
+                   "rel_diff_upper_vs_double_grid": float(np.abs(RU - U).max() / np.abs(U).max()),
+                   "rel_diff_lower_vs_double_grid": float(np.abs(RL - L).max() / np.abs(L).max()),
+                   "device_bytes_double_grid_only": bytes_dg, "device_bytes_with_reduced": cr.device_bytes(),
+                   "note": "mixed precision; 2^d shifted N-size transforms per application (M = 2N)"}
+        cr.close()
+
     # ---- grid-based composite: a 99^3 two-phase voxel image (Section 7.5 stand-in)
     image = None
     if args.image_steps > 0:
@@ -458,6 +482,7 @@ def run_ours(args, world, rank, local):
             "fp64": fp64,
             "gani": gani,
             "warm_start": warm,
+            "reduced": reduced,
             "image": image,
             "batched": batched,
             "served": served,
