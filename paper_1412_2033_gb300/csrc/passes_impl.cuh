@@ -622,6 +622,21 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
 
     cp_async_wait<1>();          // A_M(g) is in; spectra(g+1) may still be in flight
     __syncthreads();
+    if constexpr (MCT != 0) {
+      // the multiply by A_M runs inside the forward transform's first pass,
+      // which reads the inverse transform's output in natural order
+      auto mul = [&](int j, int m, C z) -> C {
+        const T a0 = ld[2 * j].valid ? sa[((2 * j) / per_row) * M + m] : T(0);
+        const T a1 = ld[2 * j + 1].valid ? sa[((2 * j + 1) / per_row) * M + m] : T(0);
+        return mk(a0 * z.x, a1 * z.y);
+      };
+      // once the first pass has read the staged A_M, its slot takes the next group's
+      auto refill = [&]() {
+        if (grp + nb < groups) issue_multiplier(grp + nb);
+        cp_async_commit();
+      };
+      fft_dif_ct_mul<-1, NL, kRowThreads, MCT>(buf, tw, mul, refill);   // ends with a barrier
+    } else {
     for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
       const int m = (NL == 1) ? u : u / NL;
@@ -634,9 +649,8 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     __syncthreads();
     if (grp + nb < groups) issue_multiplier(grp + nb);
     cp_async_commit();
-
-    if constexpr (MCT != 0) fft_dif_ct<-1, NL, kRowThreads, MCT>(buf, tw);
-    else fft_dif<-1, NL>(buf, st, npass, M, tw);
+    fft_dif<-1, NL>(buf, st, npass, M, tw);
+    }
     const T sc = T(0.5) / T(M);
     for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
