@@ -4,7 +4,7 @@
 
 namespace ghb {
 
-template ghb_status launch_col_ct_m<4374>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
-template ghb_status launch_row_ct_m<4374>(int, const RowArgs&, const FftPlan&, int, cudaStream_t);
+template ghb_status launch_col_ct_m<float, 4374>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
+template ghb_status launch_row_ct_m<float, 4374>(int, const RowArgs&, const FftPlan&, int, cudaStream_t);
 
 }  // namespace ghb

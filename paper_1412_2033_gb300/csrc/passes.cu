@@ -30,41 +30,57 @@ ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, 
 template <typename T, int NL, int MODE>
 ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size_t smem, cudaStream_t s);
 
-template <int M>
+template <typename T, int M>
 ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
-template <int M>
+template <typename T, int M>
 ghb_status launch_row_ct_m(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
 
+template <typename T>
 ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   switch (pl.M) {
-    case 162: return launch_col_ct_m<162>(sign, mode, a, pl, s);
-    case 486: return launch_col_ct_m<486>(sign, mode, a, pl, s);
-    case 1458: return launch_col_ct_m<1458>(sign, mode, a, pl, s);
-    case 4374: return launch_col_ct_m<4374>(sign, mode, a, pl, s);
-    case 2187: return launch_col_ct_m<2187>(sign, mode, a, pl, s);
+    case 162: return launch_col_ct_m<T, 162>(sign, mode, a, pl, s);
+    case 486: return launch_col_ct_m<T, 486>(sign, mode, a, pl, s);
+    case 1458: return launch_col_ct_m<T, 1458>(sign, mode, a, pl, s);
+    case 4374: return launch_col_ct_m<T, 4374>(sign, mode, a, pl, s);
+    case 2187: return launch_col_ct_m<T, 2187>(sign, mode, a, pl, s);
     default: break;
   }
   set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
   return GHB_ERR_INVALID;
 }
+template ghb_status launch_col_ct<float>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
+template ghb_status launch_col_ct<double>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 
+template <typename T>
 ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s) {
   switch (pl.M) {
-    case 162: return launch_row_ct_m<162>(NL, a, pl, rows_per_cta, s);
-    case 486: return launch_row_ct_m<486>(NL, a, pl, rows_per_cta, s);
-    case 1458: return launch_row_ct_m<1458>(NL, a, pl, rows_per_cta, s);
-    case 4374: return launch_row_ct_m<4374>(NL, a, pl, rows_per_cta, s);
-    case 2187: return launch_row_ct_m<2187>(NL, a, pl, rows_per_cta, s);
+    case 162: return launch_row_ct_m<T, 162>(NL, a, pl, rows_per_cta, s);
+    case 486: return launch_row_ct_m<T, 486>(NL, a, pl, rows_per_cta, s);
+    case 1458: return launch_row_ct_m<T, 1458>(NL, a, pl, rows_per_cta, s);
+    case 4374: return launch_row_ct_m<T, 4374>(NL, a, pl, rows_per_cta, s);
+    case 2187: return launch_row_ct_m<T, 2187>(NL, a, pl, rows_per_cta, s);
     default: break;
   }
   set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
   return GHB_ERR_INVALID;
+}
+template ghb_status launch_row_ct<float>(int, const RowArgs&, const FftPlan&, int, cudaStream_t);
+template ghb_status launch_row_ct<double>(int, const RowArgs&, const FftPlan&, int, cudaStream_t);
+
+// The size-specialised kernels run where they are compiled and the plan
+// carries their input order; FP32 follows the autotuner's choice, FP64 always
+// takes them (its passes are bound by the FP64 pipe, where the compile-time
+// roots save the most).
+template <typename T>
+bool use_ct(const FftPlan& pl, bool tuned_on) {
+  if (pl.perm_ct == nullptr || !ct_size(pl.M)) return false;
+  return sizeof(T) == 8 || tuned_on;
 }
 
 template <typename T>
 ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   using C = typename CT<T>::type;
-  if (sizeof(T) == 4 && pl.ct_col && pl.perm_ct != nullptr && ct_size(pl.M)) return launch_col_ct(sign, mode, a, pl, s);
+  if (use_ct<T>(pl, pl.ct_col != 0)) return launch_col_ct<T>(sign, mode, a, pl, s);
   const int tuned = pl.tile[sizeof(T) == 4 ? 1 : 0];
   const int TW = tuned > 0 ? tuned : col_tile_width(pl.M, sizeof(C));
   if (col_smem_bytes(pl.M, TW, sizeof(C)) > 220 * 1024) {
@@ -146,8 +162,7 @@ ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_
   int rows_per_cta = 1, NL = 1;
   row_lines(mode, a.nfields, a.ncomp, pl.M, sizeof(T) == 4 ? pl.rows32 : 0, &rows_per_cta, &NL);
   if (mode == ROW_MATVEC) {
-    if (sizeof(T) == 4 && pl.ct_row && pl.perm_ct != nullptr && ct_size(pl.M))
-      return launch_row_ct(NL, a, pl, rows_per_cta, s);
+    if (use_ct<T>(pl, pl.ct_row != 0)) return launch_row_ct<T>(NL, a, pl, rows_per_cta, s);
     switch (NL) {
       case 1: return launch_row_nl<T, 1, ROW_MATVEC>(a, pl, rows_per_cta, s);
       case 2: return launch_row_nl<T, 2, ROW_MATVEC>(a, pl, rows_per_cta, s);
