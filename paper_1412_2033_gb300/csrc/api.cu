@@ -131,7 +131,7 @@ ghb_status dmalloc(ghb_ctx* c, P** ptr, int64_t count) {
     if (s__ != GHB_OK) return s__;     \
   } while (0)
 
-FieldGeom fgeom(const Geometry& g) { return FieldGeom{g.d, {g.N[0], g.N[1], g.N[2]}, g.h, g.P}; }
+FieldGeom fgeom(const Geometry& g) { return make_field_geom(g.d, g.N[0], g.N[1], g.N[2], g.h, g.P); }
 
 const FftPlan& plan_of(const ghb_ctx* c, int axis) { return c->plan[c->plan_of_axis[axis]].plan; }
 
@@ -665,8 +665,13 @@ ghb_status set_history(ghb_ctx* c, double* hist, int cap) {
 // energy of E + e along the iterates (bound tracking, Section 7.4): FP64, every
 // CG iterate, J(x_i) = J(x_0) - sum_{j<i} alpha_j <r_j, r_j>; mixed, the start
 // and every FP64 correction, each an exact Gram evaluation.
+// With ax_out (mixed precision only), the operator output of the returned
+// iterate before projection -- left in the FP64 work buffer by the last
+// residual correction -- is copied there and *ax_ok says whether it was.
 ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_solve_info* info,
-                 const double2* x0 = nullptr, std::vector<double>* energies = nullptr) {
+                 const double2* x0 = nullptr, std::vector<double>* energies = nullptr,
+                 double2* ax_out = nullptr, bool* ax_ok = nullptr) {
+  if (ax_ok) *ax_ok = false;
   const Geometry& g = c->g;
   const FieldGeom fg = fgeom(g);
   ghb_solve_info inf{};
@@ -745,6 +750,7 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
     // projected iterate, w64.x its unprojected accumulation.
     double2* x64 = c->y64;
     double2* r64 = c->w64.r;
+    bool ax_valid = false;   // w64.w holds the unprojected operator output of x64
     // ||b||^2 through the FP64 residual kernel with y = 0
     GHB_CUDA_TRY(cudaMemsetAsync(c->w64.q, 0, sizeof(double2) * g.field, c->stream));
     PROF(c, PK_RESIDUAL, false, launch_residual(r64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
@@ -756,6 +762,7 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
       GHB_CUDA_TRY(cudaMemcpyAsync(c->w64.x, x0, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice,
                                    c->stream));
       TRY(apply_op<double2>(c, kind, x64, c->w64.q, true));
+      ax_valid = true;
       PROF(c, PK_RESIDUAL, false, launch_residual(r64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
       TRY(read_state(c));
       rr = c->h_st->rr;
@@ -787,11 +794,13 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
         break;
       }
       PROF(c, PK_MISC, false, launch_accum_f32(c->w64.x, c->w64.x, c->w32.x, fg, c->stream));
+      ax_valid = false;
       // exact FP64 projection onto the admissible (real, curl- or divergence-free) fields
       PROF(c, PK_PROJECT, false, launch_project<double>(x64, c->w64.x, fg, kind, c->stream));
       GHB_CUDA_TRY(cudaMemcpyAsync(c->w64.x, x64, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice,
                                    c->stream));
       TRY(apply_op<double2>(c, kind, x64, c->w64.q, true));
+      ax_valid = true;
       mv64 += 1;
       PROF(c, PK_RESIDUAL, false, launch_residual(r64, c->b64, c->w64.q, fg, c->st, c->partials, c->stream));
       TRY(read_state(c));
@@ -805,7 +814,13 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
         double J = 0.0;
         TRY(energy_of(c, kind, E, x64, field_out, &J));
         energies->push_back(J);
+        ax_valid = false;
       }
+    }
+    if (ax_out && ax_valid) {
+      GHB_CUDA_TRY(cudaMemcpyAsync(ax_out, c->w64.w, sizeof(double2) * g.field, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+      if (ax_ok) *ax_ok = true;
     }
     inf.iters = total_inner;
     inf.outer_iters = outer;
@@ -1441,17 +1456,39 @@ ghb_status ghb_bounds(ghb_ctx* c, double* upper, double* lower, ghb_solve_info* 
   const int d = c->g.d;
   ghb_status worst = GHB_OK;
   double G[2][9];
+  // Mixed precision: each solve ends with an FP64 operator application to its
+  // iterate, whose output before projection gives the Gram matrix on Z_N
+  // (launch_gram_zn) without the double-grid Gram passes.
+  const bool reuse = c->opt.precision == GHB_MIXED && c->op == &c->ga;
   for (int kind = 0; kind < 2; ++kind) {
+    bool all_ax = reuse;
     for (int i = 0; i < d; ++i) {
       double E[3] = {0, 0, 0};
       E[i] = 1.0;
       ghb_solve_info inf{};
-      TRY(solve(c, kind, E, c->sol[i], &inf));
+      bool ax_ok = false;
+      TRY(solve(c, kind, E, c->sol[i], &inf, nullptr, nullptr, reuse ? c->gT1[i] : nullptr,
+                &ax_ok));
+      all_ax = all_ax && ax_ok;
       if (inf.status != GHB_OK && worst == GHB_OK) worst = static_cast<ghb_status>(inf.status);
       if (infos) infos[kind * d + i] = inf;
     }
     const double2* f[3] = {c->sol[0], c->sol[1], d == 3 ? c->sol[2] : nullptr};
-    TRY(gram(c, c->ga, kind, d, f, G[kind]));
+    if (all_ax) {
+      GramZnArgs ga{};
+      for (int i = 0; i < d; ++i) {
+        ga.v[i] = c->sol[i];
+        ga.y[i] = c->gT1[i];
+      }
+      PROF(c, PK_MISC, false,
+           launch_gram_zn(ga, c->tab[kind], c->g, c->partials, kMaxPartials * 6, c->d_gram, c->stream));
+      GHB_CUDA_TRY(cudaMemcpyAsync(c->h_gram, c->d_gram, sizeof(double) * d * d, cudaMemcpyDeviceToHost,
+                                   c->stream));
+      GHB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+      for (int q = 0; q < d * d; ++q) G[kind][q] = c->h_gram[q];
+    } else {
+      TRY(gram(c, c->ga, kind, d, f, G[kind]));
+    }
     if (infos)
       for (int i = 0; i < d; ++i) infos[kind * d + i].energy = G[kind][i * d + i];
   }
@@ -1528,6 +1565,8 @@ ghb_status ghb_prolong(int d, const int* Nc, const void* xc_dev, const int* Nf, 
     fc.P *= Nc[a];
     ff.P *= Nf[a];
   }
+  fc = make_field_geom(d, fc.N[0], fc.N[1], fc.N[2], fc.h, fc.P);
+  ff = make_field_geom(d, ff.N[0], ff.N[1], ff.N[2], ff.h, ff.P);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY(launch_prolong(static_cast<double2*>(xf_dev), ff, static_cast<const double2*>(xc_dev), fc, s));
   GHB_CUDA_TRY(cudaStreamSynchronize(s));

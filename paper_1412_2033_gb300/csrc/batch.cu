@@ -106,7 +106,7 @@ struct PlanEntry {
   FftPlan* d_plan = nullptr;
 };
 
-FieldGeom fgeom_of(const Geometry& g) { return FieldGeom{g.d, {g.N[0], g.N[1], g.N[2]}, g.h, g.P}; }
+FieldGeom fgeom_of(const Geometry& g) { return make_field_geom(g.d, g.N[0], g.N[1], g.N[2], g.h, g.P); }
 
 // Work-item arrays of the launches of one phase: appended to a pinned host
 // buffer, copied to the device with one transfer (flush) before the launches

@@ -232,13 +232,15 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw, const 
   }
 }
 
-template <int SIGN, int NL, int NT, int M, int I, typename C>
+// Decimation-in-time passes I .. HI-1 (HI < 0: through the last pass).
+template <int SIGN, int NL, int NT, int M, int I, int HI = -1, typename C>
 __device__ __forceinline__ void ct_dit_from(C* buf, const C* __restrict__ tw) {
   constexpr CtPlan P = ct_plan(M);
-  if constexpr (I < P.npass) {
+  constexpr int E = HI < 0 ? P.npass : HI;
+  if constexpr (I < E) {
     ct_pass<SIGN, true, NL, NT, M, P.lp[I], P.ra[I], P.rb[I], P.rc[I]>(buf, tw);
     __syncthreads();
-    ct_dit_from<SIGN, NL, NT, M, I + 1>(buf, tw);
+    ct_dit_from<SIGN, NL, NT, M, I + 1, HI>(buf, tw);
   }
 }
 
@@ -293,6 +295,60 @@ __device__ __forceinline__ void fft_dif_ct_mul(C* buf, const C* __restrict__ tw,
   __syncthreads();
   after_first();
   ct_dif_from<SIGN, NL, NT, M, I - 1>(buf, tw);
+}
+
+// Inverse transform of each line (decimation in time, input from src in the
+// first pass), pointwise scaling, forward transform (decimation in frequency).
+// The inverse's last pass and the forward's first pass act on the same
+// entries p + j LP of the natural order (b = 0 in both), so one thread does
+// both in registers with mul(line, m, v) in between: one shared-memory round
+// trip and one barrier fewer per line.  Hooks: after_first() once the
+// inverse's first pass is done in every thread (src is no longer read);
+// before_fused() ahead of the fused pass (mul's data must be in place);
+// after_fused() once the fused pass is done in every thread.  Needs two
+// passes at least; ends with a barrier.
+template <int SIGN_I, int SIGN_F, int NL, int NT, int M, typename C, typename Src, typename Mul, typename H1,
+          typename H2, typename H3>
+__device__ __forceinline__ void ct_inverse_scale_forward(C* buf, const C* __restrict__ tw, const Src& src,
+                                                         const Mul& mul, const H1& after_first,
+                                                         const H2& before_fused, const H3& after_fused) {
+  constexpr CtPlan P = ct_plan(M);
+  static_assert(P.ok && P.npass >= 2, "the fused pass needs a transform of two passes at least");
+  constexpr int I = P.npass - 1;
+  constexpr int LP = P.lp[I], RA = P.ra[I], RB = P.rb[I], RC = P.rc[I];
+  constexpr int RG = RA * RB * RC;
+  static_assert(LP * RG == M, "the last pass spans the line");
+  constexpr int tsA = M / (LP * RA);
+  constexpr int tsB = tsA / RB;
+  constexpr int tsC = tsB / RC;
+  constexpr int step = LP * NL;
+  ct_pass<SIGN_I, true, NL, NT, M, 1, P.ra[0], P.rb[0], P.rc[0]>(buf, tw, src);
+  __syncthreads();
+  after_first();
+  ct_dit_from<SIGN_I, NL, NT, M, 1, I>(buf, tw);
+  before_fused();
+#pragma unroll 1
+  for (int u = threadIdx.x; u < LP * NL; u += NT) {
+    const int line = (NL == 1) ? 0 : u % NL;
+    const int p = (NL == 1) ? u : u / NL;
+    C* base = buf + p * NL + line;
+    C v[RG];
+#pragma unroll
+    for (int j = 0; j < RG; ++j) v[j] = base[j * step];
+    ct_substage<SIGN_I, true, false, RA, 1, RG, tsA>(v, p, tw);
+    if constexpr (RB > 1) ct_substage<SIGN_I, true, false, RB, RA, RG, tsB>(v, p, tw);
+    if constexpr (RC > 1) ct_substage<SIGN_I, true, false, RC, RA * RB, RG, tsC>(v, p, tw);
+#pragma unroll
+    for (int j = 0; j < RG; ++j) v[j] = mul(line, p + j * LP, v[j]);
+    if constexpr (RC > 1) ct_substage<SIGN_F, false, false, RC, RA * RB, RG, tsC>(v, p, tw);
+    if constexpr (RB > 1) ct_substage<SIGN_F, false, false, RB, RA, RG, tsB>(v, p, tw);
+    ct_substage<SIGN_F, false, false, RA, 1, RG, tsA>(v, p, tw);
+#pragma unroll
+    for (int j = 0; j < RG; ++j) base[j * step] = v[j];
+  }
+  __syncthreads();
+  after_fused();
+  ct_dif_from<SIGN_F, NL, NT, M, I - 1>(buf, tw);
 }
 
 // The same with every output handed to snk(line, n, value), n the natural

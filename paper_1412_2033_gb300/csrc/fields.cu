@@ -29,7 +29,7 @@ __device__ __forceinline__ void kvec(const FieldGeom& g, int64_t e64, int k[3], 
   // 32-bit index arithmetic: a field has fewer than 2^31 entries per component
   const unsigned e = static_cast<unsigned>(e64);
   const unsigned h = static_cast<unsigned>(g.h);
-  const unsigned i12 = e / h;
+  const unsigned i12 = fdiv(e, g.hdiv);
   j = static_cast<int>(e - i12 * h);
   if (g.d == 2) {
     k[0] = static_cast<int>(i12) - (g.N[0] - 1) / 2;
@@ -37,12 +37,18 @@ __device__ __forceinline__ void kvec(const FieldGeom& g, int64_t e64, int k[3], 
     k[2] = 0;
   } else {
     const unsigned n1 = static_cast<unsigned>(g.N[1]);
-    const unsigned i1 = i12 / n1;
+    const unsigned i1 = fdiv(i12, g.n1div);
     const unsigned i2 = i12 - i1 * n1;
     k[0] = static_cast<int>(i1) - (g.N[0] - 1) / 2;
     k[1] = static_cast<int>(i2) - (g.N[1] - 1) / 2;
     k[2] = j;
   }
+}
+
+// Last-axis frequency j of entry e (e mod h).
+__device__ __forceinline__ int jindex(const FieldGeom& g, int64_t e64) {
+  const unsigned e = static_cast<unsigned>(e64);
+  return static_cast<int>(e - fdiv(e, g.hdiv) * static_cast<unsigned>(g.h));
 }
 
 // Index of the entry holding -k for an entry on the plane k_d = 0 (where both
@@ -83,8 +89,9 @@ __device__ __forceinline__ void project_vec(int d, const int k[3], int kind, con
     sx += kv[c] * w[c].x;
     sy += kv[c] * w[c].y;
   }
-  sx /= kk;
-  sy /= kk;
+  const T inv = T(1) / kk;   // one division per entry
+  sx *= inv;
+  sy *= inv;
   for (int c = 0; c < d; ++c) {
     const C pe = mk(kv[c] * sx, kv[c] * sy);
     q[c] = (kind == GHB_PRIMAL) ? pe : mk(w[c].x - pe.x, w[c].y - pe.y);
@@ -282,9 +289,12 @@ __global__ void rhs_kernel(double2* b, const double2* tab, Geometry g, FieldGeom
   for (int64_t e = (bid) * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < (fg).P; \
        e += (nb) * static_cast<int64_t>(blockDim.x))
 
+// The per-entry loops below take the dimension as a template parameter D so
+// that the component arrays stay in registers.
+
 // q = G w (with the Hermitian part taken on k_d = 0); q must not alias w.
-template <typename T>
-__device__ void op_project(const CgItem& it, int64_t bid, int64_t nb) {
+template <typename T, int D>
+__device__ __forceinline__ void project_loop(const CgItem& it, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
   const FieldGeom& fg = it.fg;
   const C* w = static_cast<const C*>(it.w);
@@ -294,11 +304,18 @@ __device__ void op_project(const CgItem& it, int64_t bid, int64_t nb) {
     int j;
     kvec(fg, e, k, j);
     const int64_t em = mirror_index(fg, k, j);
-    C wv[3], q[3];
-    for (int c = 0; c < fg.d; ++c) wv[c] = hermitian_part(w, fg.P, c, e, em);
-    project_vec<T>(fg.d, k, it.kind, wv, q);
-    for (int c = 0; c < fg.d; ++c) y[c * fg.P + e] = q[c];
+    C wv[D], q[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) wv[c] = hermitian_part(w, fg.P, c, e, em);
+    project_vec<T>(D, k, it.kind, wv, q);
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c * fg.P + e] = q[c];
   }
+}
+template <typename T>
+__device__ void op_project(const CgItem& it, int64_t bid, int64_t nb) {
+  if (it.fg.d == 2) project_loop<T, 2>(it, bid, nb);
+  else project_loop<T, 3>(it, bid, nb);
 }
 
 // x = 0, r = b, p = 0, <b, b>; the last block initialises the CG scalars.
@@ -315,7 +332,7 @@ __device__ void op_init(const CgItem& it, int64_t bid, int64_t nb) {
   // cross-thread and cross-block sums in FP64
   T acc = T(0);
   GHB_FIELD_LOOP(e, fg, bid, nb) {
-    const int j = static_cast<int>(static_cast<unsigned>(e) % static_cast<unsigned>(fg.h));
+    const int j = jindex(fg, e);
     const T wt = (j == 0) ? T(1) : T(2);
     for (int c = 0; c < fg.d; ++c) {
       const int64_t i = c * fg.P + e;
@@ -342,34 +359,47 @@ __device__ void op_init(const CgItem& it, int64_t bid, int64_t nb) {
   }
 }
 
-// q = G w, <p, q>; the last block forms alpha = <r, r> / <p, A p>.
-template <typename T>
-__device__ void op_project_dot(const CgItem& it, int64_t bid, int64_t nb) {
+// Per-thread part of op_project_dot: q = G w on this thread's entries and
+// their share of <p, q> (in the field's precision).
+template <typename T, int D>
+__device__ __forceinline__ T project_dot_loop(const CgItem& it, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
   const FieldGeom& fg = it.fg;
-  CgState* st = it.st;
-  if (st->done != RUNNING) return;
   C* q = static_cast<C*>(it.q);
   const C* w = static_cast<const C*>(it.w);
   const C* p = static_cast<const C*>(it.p);
-  T acc = T(0);   // per-thread partial in the field's precision, FP64 across threads
+  T acc = T(0);
   GHB_FIELD_LOOP(e, fg, bid, nb) {
     int k[3];
     int j;
     kvec(fg, e, k, j);
     const T wt = (j == 0) ? T(1) : T(2);
     const int64_t em = mirror_index(fg, k, j);
-    C wv[3], qv[3];
-    for (int c = 0; c < fg.d; ++c) wv[c] = hermitian_part(w, fg.P, c, e, em);
-    project_vec<T>(fg.d, k, it.kind, wv, qv);
+    C wv[D], pv[D], qv[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      wv[c] = hermitian_part(w, fg.P, c, e, em);
+      pv[c] = p[c * fg.P + e];
+    }
+    project_vec<T>(D, k, it.kind, wv, qv);
     T sacc = T(0);
-    for (int c = 0; c < fg.d; ++c) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
       q[c * fg.P + e] = qv[c];
-      const C pv = p[c * fg.P + e];
-      sacc += pv.x * qv[c].x + pv.y * qv[c].y;
+      sacc += pv[c].x * qv[c].x + pv[c].y * qv[c].y;
     }
     acc += wt * sacc;
   }
+  return acc;
+}
+
+// q = G w, <p, q>; the last block forms alpha = <r, r> / <p, A p>.
+template <typename T>
+__device__ void op_project_dot(const CgItem& it, int64_t bid, int64_t nb) {
+  const FieldGeom& fg = it.fg;
+  CgState* st = it.st;
+  if (st->done != RUNNING) return;
+  const T acc = fg.d == 2 ? project_dot_loop<T, 2>(it, bid, nb) : project_dot_loop<T, 3>(it, bid, nb);
   double tot;
   if (grid_sum_last(static_cast<double>(acc), it.partials, &st->ticket, &tot, bid, nb)) {
     st->pq = tot;
@@ -382,33 +412,51 @@ __device__ void op_project_dot(const CgItem& it, int64_t bid, int64_t nb) {
   }
 }
 
-// x += alpha p, r -= alpha q, <r, r>; the last block forms beta and the stop test.
-template <typename T>
-__device__ void op_update(const CgItem& it, int64_t bid, int64_t nb) {
+// Per-thread part of op_update: x += alpha p, r -= alpha q on this thread's
+// entries and their share of <r, r>.
+template <typename T, int D>
+__device__ __forceinline__ T update_loop(const CgItem& it, T al, int64_t bid, int64_t nb) {
   using C = typename CT<T>::type;
   const FieldGeom& fg = it.fg;
-  CgState* st = it.st;
-  if (st->done != RUNNING) return;
   C* x = static_cast<C*>(it.x);
   C* r = static_cast<C*>(it.r);
   const C* p = static_cast<const C*>(it.p);
   const C* q = static_cast<const C*>(it.q);
-  const T al = static_cast<T>(st->alpha);
-  T acc = T(0);   // per-thread partial in the field's precision, FP64 across threads
+  T acc = T(0);
   GHB_FIELD_LOOP(e, fg, bid, nb) {
-    const int j = static_cast<int>(static_cast<unsigned>(e) % static_cast<unsigned>(fg.h));
+    const int j = jindex(fg, e);
     const T wt = (j == 0) ? T(1) : T(2);
-    for (int c = 0; c < fg.d; ++c) {
+    C pv[D], qv[D], xv[D], rv[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
       const int64_t i = c * fg.P + e;
-      const C pv = p[i], qv = q[i];
-      C xv = x[i], rv = r[i];
-      xv = mk(xv.x + al * pv.x, xv.y + al * pv.y);
-      rv = mk(rv.x - al * qv.x, rv.y - al * qv.y);
-      x[i] = xv;
-      r[i] = rv;
-      acc += wt * (rv.x * rv.x + rv.y * rv.y);
+      pv[c] = p[i];
+      qv[c] = q[i];
+      xv[c] = x[i];
+      rv[c] = r[i];
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const int64_t i = c * fg.P + e;
+      const C xn = mk(xv[c].x + al * pv[c].x, xv[c].y + al * pv[c].y);
+      const C rn = mk(rv[c].x - al * qv[c].x, rv[c].y - al * qv[c].y);
+      x[i] = xn;
+      r[i] = rn;
+      acc += wt * (rn.x * rn.x + rn.y * rn.y);
     }
   }
+  return acc;
+}
+
+// x += alpha p, r -= alpha q, <r, r>; the last block forms beta and the stop test.
+template <typename T>
+__device__ void op_update(const CgItem& it, int64_t bid, int64_t nb) {
+  const FieldGeom& fg = it.fg;
+  CgState* st = it.st;
+  if (st->done != RUNNING) return;
+  const T al = static_cast<T>(st->alpha);
+  // per-thread partial in the field's precision, FP64 across threads
+  const T acc = fg.d == 2 ? update_loop<T, 2>(it, al, bid, nb) : update_loop<T, 3>(it, al, bid, nb);
   double tot;
   if (grid_sum_last(static_cast<double>(acc), it.partials, &st->ticket, &tot, bid, nb)) {
     const double rr_old = st->rr;
@@ -431,7 +479,7 @@ __device__ void op_residual(const CgItem& it, int64_t bid, int64_t nb) {
   const double2* y = static_cast<const double2*>(it.w);
   double acc = 0.0;
   GHB_FIELD_LOOP(e, fg, bid, nb) {
-    const int j = static_cast<int>(static_cast<unsigned>(e) % static_cast<unsigned>(fg.h));
+    const int j = jindex(fg, e);
     const double wt = (j == 0) ? 1.0 : 2.0;
     for (int c = 0; c < fg.d; ++c) {
       const int64_t i = c * fg.P + e;
@@ -542,7 +590,7 @@ template <typename T>
 ghb_status launch_rhs(void* b, const double2* tab, const Geometry& g, const double* E, int kind,
                       cudaStream_t s) {
   static_assert(sizeof(T) == 8, "the right-hand side is formed in FP64");
-  FieldGeom fg{g.d, {g.N[0], g.N[1], g.N[2]}, g.h, g.P};
+  const FieldGeom fg = make_field_geom(g.d, g.N[0], g.N[1], g.N[2], g.h, g.P);
   const double3 Ev = make_double3(E[0], E[1], g.d == 3 ? E[2] : 0.0);
   rhs_kernel<<<field_grid(g.P), kFieldThreads, 0, s>>>(static_cast<double2*>(b), tab, g, fg, Ev, kind);
   GHB_CUDA_TRY(cudaGetLastError());
@@ -550,6 +598,90 @@ ghb_status launch_rhs(void* b, const double2* tab, const Geometry& g, const doub
 }
 template ghb_status launch_rhs<double>(void*, const double2*, const Geometry&, const double*, int,
                                        cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Gram matrix on Z_N (Lemma FD_matrix_full): for admissible fields
+// v_i = E_i + x_i (E_i the i-th unit load),
+//   X_ij = Re sum_{k in Z_N} (A v_i)^(k) . conj v_j(k),
+// where (A v_i)^(k) = a^(k) E_i + y_i(k) and y_i is the operator output of x_i
+// before the projection (pad, inverse transform, A_M, forward transform,
+// truncation to Z_N).  v_j vanishes outside Z_N, so this is the exact energy
+// the double-grid evaluation gives.  Per-block partial sums of the d^2 entries
+// in FP64, then one block adds the partials in block order.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kFieldThreads) gram_zn_kernel(GramZnArgs ga, const double2* __restrict__ tab,
+                                                                Geometry g, FieldGeom fg, double* partials) {
+  __shared__ double red[32];
+  const int Ld = g.N[D - 1];
+  const int L1 = 2 * g.N[1] - 1;
+  double acc[D * D];
+#pragma unroll
+  for (int q = 0; q < D * D; ++q) acc[q] = 0.0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int k[3];
+    int j;
+    kvec(fg, e, k, j);
+    const double wt = (j == 0) ? 1.0 : 2.0;
+    int64_t ti;
+    if (D == 2) ti = static_cast<int64_t>(k[0] + g.N[0] - 1) * Ld + j;
+    else ti = (static_cast<int64_t>(k[0] + g.N[0] - 1) * L1 + (k[1] + g.N[1] - 1)) * Ld + j;
+    const double2 a = tab[ti];
+    double2 v[D][D], y[D][D];   // [field][component]
+#pragma unroll
+    for (int f = 0; f < D; ++f)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        v[f][c] = ga.v[f][c * fg.P + e];
+        y[f][c] = ga.y[f][c * fg.P + e];
+      }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      // (A v_i)^(k): y_i plus a^(k) in component i
+      double2 av[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) av[c] = (c == i) ? make_double2(y[i][c].x + a.x, y[i][c].y + a.y) : y[i][c];
+#pragma unroll
+      for (int jf = 0; jf < D; ++jf) {
+        double sre = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) sre += av[c].x * v[jf][c].x + av[c].y * v[jf][c].y;
+        acc[i * D + jf] += wt * sre;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < D * D; ++q) {
+    const double bs = block_sum(acc[q], red);
+    if (threadIdx.x == 0) partials[static_cast<int64_t>(q) * gridDim.x + blockIdx.x] = bs;
+  }
+}
+
+__global__ void __launch_bounds__(kFieldThreads) gram_zn_final(const double* __restrict__ partials, int nb, int dd,
+                                                               double* out) {
+  __shared__ double red[32];
+  for (int q = 0; q < dd; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[static_cast<int64_t>(q) * nb + b];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[q] = s;
+  }
+}
+
+ghb_status launch_gram_zn(const GramZnArgs& ga, const double2* tab, const Geometry& g, double* partials,
+                          int max_partials, double* out, cudaStream_t s) {
+  const FieldGeom fg = make_field_geom(g.d, g.N[0], g.N[1], g.N[2], g.h, g.P);
+  const int dd = g.d * g.d;
+  int nb = field_grid(g.P);
+  if (nb * dd > max_partials) nb = max_partials / dd;
+  if (g.d == 2) gram_zn_kernel<2><<<nb, kFieldThreads, 0, s>>>(ga, tab, g, fg, partials);
+  else gram_zn_kernel<3><<<nb, kFieldThreads, 0, s>>>(ga, tab, g, fg, partials);
+  GHB_CUDA_TRY(cudaGetLastError());
+  gram_zn_final<<<1, kFieldThreads, 0, s>>>(partials, nb, dd, out);
+  GHB_CUDA_TRY(cudaGetLastError());
+  return GHB_OK;
+}
 
 namespace {
 template <typename T, int OP>

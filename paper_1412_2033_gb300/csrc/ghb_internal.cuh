@@ -197,7 +197,25 @@ struct FieldGeom {
   int N[3];
   int h;
   int64_t P;
+  FastDiv hdiv;    // division by h (entry index -> row, j)
+  FastDiv n1div;   // division by N[1] (row -> i_1, i_2 for d = 3)
 };
+
+// Field geometry with its divisors: the field kernels split an entry index
+// into (row, j) and a row into (i_1, i_2) by multiply-high division, since a
+// run-time integer division costs tens of instructions per entry.
+inline FieldGeom make_field_geom(int d, int N0, int N1, int N2, int h, int64_t P) {
+  FieldGeom f;
+  f.d = d;
+  f.N[0] = N0;
+  f.N[1] = N1;
+  f.N[2] = N2;
+  f.h = h;
+  f.P = P;
+  f.hdiv = make_fastdiv(static_cast<unsigned>(h > 0 ? h : 1));
+  f.n1div = make_fastdiv(static_cast<unsigned>(N1 > 0 ? N1 : 1));
+  return f;
+}
 
 ghb_status launch_coeff_table(double2* tab, const Geometry& g, const Incl* incs, int n, double a0v,
                               cudaStream_t s);
@@ -216,6 +234,16 @@ template <typename T>
 ghb_status launch_update(void* x, void* r, const void* p, const void* q, const FieldGeom& fg,
                          CgState* st, double* partials, cudaStream_t s);
 // r64 = b64 - y64, rr into st (FP64 outer residual); also st->done reset
+// Fields of a Gram matrix on Z_N: v[i] = E_i + x_i (admissible fields, with
+// the load at k = 0) and y[i] the operator output of x_i before projection.
+struct GramZnArgs {
+  const double2* v[3];
+  const double2* y[3];
+};
+// X_ij = Re sum_{k in Z_N} (a^ E_i + y_i)(k) . conj v_j(k) (d x d, row-major)
+// into out (device, d^2 doubles); partials holds max_partials doubles.
+ghb_status launch_gram_zn(const GramZnArgs& ga, const double2* tab, const Geometry& g, double* partials,
+                          int max_partials, double* out, cudaStream_t s);
 ghb_status launch_residual(double2* r, const double2* b, const double2* y, const FieldGeom& fg,
                            CgState* st, double* partials, cudaStream_t s);
 ghb_status launch_to_f32(float2* dst, const double2* src, const FieldGeom& fg, cudaStream_t s);
@@ -293,13 +321,15 @@ __host__ __device__ constexpr int col_tile_width(int M, int elem_bytes) {
   return 1;
 }
 
-// Transform lengths with size-specialised FP32 operator kernels (fft_ct.cuh):
-// the double grids 2 * 3^k of the 2-D operator at N = 81, 243, 729, 2187, and
-// 2187 itself (the reduced operator's transforms at N = 2187).
+// Transform lengths with size-specialised FP32 and FP64 operator kernels
+// (fft_ct.cuh): the double grids 2 * 3^k of the 2-D operator at N = 81, 243,
+// 729, 2187, and 2187 itself (the reduced operator's transforms at N = 2187).
 __host__ __device__ constexpr bool ct_size(int M) {
   return M == 162 || M == 486 || M == 1458 || M == 4374 || M == 2187;
 }
+template <typename T>
 ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
+template <typename T>
 ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
 
 }  // namespace ghb

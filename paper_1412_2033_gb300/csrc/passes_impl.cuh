@@ -53,9 +53,12 @@ __device__ __forceinline__ int bix(int i) {
 }
 
 // Threads of a column-pass CTA.
+// FP64 size-specialised transforms hold a radix group of up to 27 complex
+// doubles per thread, which needs more than the 128 registers a 512-thread CTA
+// allows.
 template <typename T, int TW, int MCT>
 __host__ __device__ constexpr int col_threads() {
-  if constexpr (MCT != 0) return MCT * TW >= 2048 ? 512 : 256;
+  if constexpr (MCT != 0) return (sizeof(T) == 4 && MCT * TW >= 2048) ? 512 : 256;
   else return sizeof(T) == 8 ? 256 : 512;
 }
 
@@ -66,6 +69,10 @@ __host__ __device__ constexpr int col_threads() {
 // line t is input row i(n) = n + half (n <= half) or n - M + half
 // (n >= M - half), zero in between; with UPDATE the entry is r + beta p_old
 // and is written back to p_new once all of a unit's entries are loaded.
+// The pointers are offset to (row half, column j0) of the tile, so an entry's
+// offset |r| inner + t stays within one component's field and fits 32 bits
+// (a 64-bit index per loaded entry would hold two registers each until the
+// write-back).
 template <typename C, typename T, bool UPDATE>
 struct ColSource {
   static constexpr bool kWriteBack = UPDATE;
@@ -73,17 +80,16 @@ struct ColSource {
   const C* __restrict__ pold;
   C* __restrict__ pnew;
   T beta;
-  int64_t base;     // index of (row half, column j0) of this tile
-  int64_t inner;    // row stride
+  int inner;        // row stride
   int half, M, width;
-  __device__ __forceinline__ int64_t index(int t, int n, bool& ok) const {
+  __device__ __forceinline__ int index(int t, int n, bool& ok) const {
     const int r = n <= half ? n : (n >= M - half ? n - M : M);   // row offset from the centre
     ok = r != M && t < width;
-    return base + static_cast<int64_t>(r) * inner + t;
+    return r * inner + t;
   }
   __device__ __forceinline__ C operator()(int t, int n) const {
     bool ok;
-    const int64_t idx = index(t, n, ok);
+    const int idx = index(t, n, ok);
     C v = mk(T(0), T(0));
     if (ok) {
       v = in[idx];
@@ -96,7 +102,7 @@ struct ColSource {
   }
   __device__ __forceinline__ void write_back(int t, int n, C v) const {
     bool ok;
-    const int64_t idx = index(t, n, ok);
+    const int idx = index(t, n, ok);
     if (ok) pnew[idx] = v;
   }
 };
@@ -128,8 +134,15 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
     const int half = (Lin - 1) / 2;
     T beta = T(0);
     if constexpr (MODE == COL_PUPDATE) beta = static_cast<T>(a.st->beta);
-    ColSource<C, T, MODE == COL_PUPDATE> src{in, static_cast<const C*>(a.pold), static_cast<C*>(a.pnew), beta,
-                                            (o * Lin + half) * a.inner + j0, a.inner, half, M, width};
+    const int64_t base = (o * Lin + half) * a.inner + j0;   // (row half, column j0) of this tile
+    const C* pold = nullptr;
+    C* pnew = nullptr;
+    if constexpr (MODE == COL_PUPDATE) {
+      pold = static_cast<const C*>(a.pold) + base;
+      pnew = static_cast<C*>(a.pnew) + base;
+    }
+    ColSource<C, T, MODE == COL_PUPDATE> src{in + base, pold, pnew, beta, static_cast<int>(a.inner), half, M,
+                                            width};
     fft_dit_ct_src<+1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, src);
     C* __restrict__ out = static_cast<C*>(a.out);
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
@@ -598,8 +611,26 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
         if ((lo || hi) && ld[2 * j + 1].valid) B = sin[(2 * j + 1) * H + k];
         return lo ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
       };
-      fft_dit_ct_src<+1, NL, kRowThreads, MCT>(buf, tw, src);   // ends with a barrier
-      if (grp + nb < groups) issue_spectra(grp + nb);            // staging is free again
+      // multiply by A_M between the transforms, in registers
+      auto mul = [&](int j, int m, C z) -> C {
+        const T a0 = ld[2 * j].valid ? sa[((2 * j) / per_row) * M + m] : T(0);
+        const T a1 = ld[2 * j + 1].valid ? sa[((2 * j + 1) / per_row) * M + m] : T(0);
+        return mk(a0 * z.x, a1 * z.y);
+      };
+      auto after_first = [&]() {   // the staged spectra are read: stage the next group's
+        if (grp + nb < groups) issue_spectra(grp + nb);
+        cp_async_commit();
+      };
+      auto before_fused = [&]() {  // A_M(g) is in; spectra(g+1) may still be in flight
+        cp_async_wait<1>();
+        __syncthreads();
+      };
+      auto after_fused = [&]() {   // the staged A_M is read: stage the next group's
+        if (grp + nb < groups) issue_multiplier(grp + nb);
+        cp_async_commit();
+      };
+      ct_inverse_scale_forward<+1, -1, NL, kRowThreads, MCT>(buf, tw, src, mul, after_first, before_fused,
+                                                             after_fused);   // ends with a barrier
     } else {
     for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
@@ -617,26 +648,10 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     __syncthreads();
     if (grp + nb < groups) issue_spectra(grp + nb);   // staging is free again
     fft_dit<+1, NL>(buf, st, npass, M, tw);
-    }
     cp_async_commit();
 
     cp_async_wait<1>();          // A_M(g) is in; spectra(g+1) may still be in flight
     __syncthreads();
-    if constexpr (MCT != 0) {
-      // the multiply by A_M runs inside the forward transform's first pass,
-      // which reads the inverse transform's output in natural order
-      auto mul = [&](int j, int m, C z) -> C {
-        const T a0 = ld[2 * j].valid ? sa[((2 * j) / per_row) * M + m] : T(0);
-        const T a1 = ld[2 * j + 1].valid ? sa[((2 * j + 1) / per_row) * M + m] : T(0);
-        return mk(a0 * z.x, a1 * z.y);
-      };
-      // once the first pass has read the staged A_M, its slot takes the next group's
-      auto refill = [&]() {
-        if (grp + nb < groups) issue_multiplier(grp + nb);
-        cp_async_commit();
-      };
-      fft_dif_ct_mul<-1, NL, kRowThreads, MCT>(buf, tw, mul, refill);   // ends with a barrier
-    } else {
     for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
       const int m = (NL == 1) ? u : u / NL;
@@ -753,19 +768,19 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
   return GHB_OK;
 }
 
-// Size-specialised FP32 operator passes for one transform length M
-// (instantiated in the ct_*.cu units).
-template <int M>
+// Size-specialised operator passes for one precision and transform length M
+// (instantiated in the ct_*.cu units for FP32 and the ct64_*.cu units for FP64).
+template <typename T, int M>
 ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
-  constexpr int TW = col_tile_width(M, 8);
-  return launch_col_tw<float, TW, M>(sign, mode, a, pl, s);
+  constexpr int TW = col_tile_width(M, 2 * sizeof(T));
+  return launch_col_tw<T, TW, M>(sign, mode, a, pl, s);
 }
-template <int M>
+template <typename T, int M>
 ghb_status launch_row_ct_m(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s) {
   switch (NL) {
-    case 1: return launch_row_t<float, 1, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
-    case 2: return launch_row_t<float, 2, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
-    case 3: return launch_row_t<float, 3, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
+    case 1: return launch_row_t<T, 1, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
+    case 2: return launch_row_t<T, 2, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
+    case 3: return launch_row_t<T, 3, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
     default: break;
   }
   set_error("internal: unsupported row-pass line count");

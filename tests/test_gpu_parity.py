@@ -192,6 +192,31 @@ def test_bounds_mixed_parity_and_one_sided(ghb, name):
     assert any(i["matvecs_fp32"] > 0 for i in infos)
 
 
+@pytest.mark.parametrize("name", ["d2_disk_ragged", "d2_square_M29", "d3_sphere_box"])
+def test_mixed_gram_on_zn_matches_double_grid(ghb, name):
+    """The mixed path forms its Gram matrices on Z_N from the final FP64
+    residual application (unprojected operator output of each iterate plus
+    a^(k) E_i); the same fields (the solves are deterministic) through the
+    double-grid Gram passes give the same matrices to FP64 rounding."""
+    spec = MICROS[name]
+    d = spec["d"]
+    ctx = make_ctx(ghb, spec, tol=1e-10, precision="mixed")
+    U, L, infos, st = ctx.bounds()
+    assert st == 0
+    G = {}
+    for kind in (ghb.GHB_PRIMAL, ghb.GHB_DUAL):
+        fields = []
+        for i in range(d):
+            f, info, _, s = ctx.solve_ex(np.eye(d)[i], kind=kind)
+            assert s == 0
+            assert abs(info["energy"] - infos[kind * d + i]["energy"]) < 1e-13 * abs(info["energy"])
+            fields.append(f)
+        X = np.asarray(ctx.gram(kind, fields))
+        G[kind] = 0.5 * (X + X.T)
+    assert rel(U, G[ghb.GHB_PRIMAL]) < 1e-13
+    assert rel(L, np.linalg.inv(G[ghb.GHB_DUAL])) < 1e-12
+
+
 def test_homogeneous_and_trivial_order(ghb):
     ctx = ghb.Context(2, [9, 9], 3.5, [])
     U, L, infos, st = ctx.bounds()
