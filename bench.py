@@ -614,8 +614,7 @@ def traffic_for(kernel_name):
 # M = 4374) and every header it includes
 TRAFFIC_SOURCES = ["paper_1412_2033_gb300/csrc/ct_4374.cu", "paper_1412_2033_gb300/csrc/passes_impl.cuh",
                    "paper_1412_2033_gb300/csrc/fft_ct.cuh", "paper_1412_2033_gb300/csrc/fft.cuh",
-                   "paper_1412_2033_gb300/csrc/ghb_internal.cuh", "paper_1412_2033_gb300/csrc/reduce.cuh",
-                   "include/ghb.h"]
+                   "paper_1412_2033_gb300/csrc/ghb_internal.cuh", "paper_1412_2033_gb300/csrc/reduce.cuh"]
 
 
 def sources_digest():

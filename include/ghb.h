@@ -364,8 +364,10 @@ ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* gri
  * they compute).  Per transform length M the library holds
  *   cfg[0] cap32   largest radix product of one register-blocked pass of the
  *                  runtime-plan FP32 transform (5..32)
- *   cfg[1] tile32  columns per CTA of the FP32 column passes (0 = size rule,
- *                  else 1, 2, 4, 8 or 16 within shared memory)
+ *   cfg[1] tile32  columns per CTA of the FP32 column passes (0 = chosen at
+ *                  each launch from the operand's shape: the widest tile whose
+ *                  CTAs fill the device three times over; else 1, 2, 4, 8 or 16
+ *                  within shared memory, forced)
  *   cfg[2] rows32  rows per CTA of the FP32 2-D last-axis pass (0 = size rule,
  *                  1 or 2)
  *   cfg[3] ct_col  1: size-specialised FP32 column kernels (only for lengths
@@ -373,8 +375,9 @@ ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* gri
  *   cfg[4] ct_row  the same for the last-axis pass
  *   cfg[5] cap64   as cap32 for FP64
  *   cfg[6] tile64  as tile32 for FP64
- * The first plan for M in a process times the candidates on a square 2-D
- * operand with CUDA events and keeps the fastest (the autotuner); setting the
+ * The first plan for M in a process times the candidates for cfg[0], [2], [3],
+ * [4] and [5] on a 2-D operand of at least 2^20 double-grid entries with CUDA
+ * events and keeps the fastest (the autotuner; the tiles stay 0); setting the
  * environment variable GHB_AUTOTUNE=0 keeps the size rules instead.  Every
  * configuration computes the same operator; results differ only by rounding.
  * A configuration applies to plans made after it is fixed (contexts and batch

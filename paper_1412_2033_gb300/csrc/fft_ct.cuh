@@ -176,13 +176,10 @@ struct ct_writes_back<S, std::void_t<decltype(S::kWriteBack)>> : std::integral_c
 // returns input n, so the caller's scatter into digit-reversed order and its
 // zero padding disappear) and may hand its results to a sink instead of the
 // buffer (DIF: snk(line, n, value) receives output n).
-// A pass may also scale every entry it loads from the buffer: mul(line, m, v)
-// returns the value to transform for entry m (the entry's index within its
-// line; natural order in the last DIT pass and the first DIF pass).
 template <int SIGN, bool DIT, int NL, int NT, int M, int LP, int RA, int RB, int RC, typename C,
-          typename Src = CtBuf, typename Snk = CtBuf, typename Mul = CtBuf>
+          typename Src = CtBuf, typename Snk = CtBuf>
 __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw, const Src& src = Src(),
-                                        const Snk& snk = Snk(), const Mul& mul = Mul()) {
+                                        const Snk& snk = Snk()) {
   constexpr int RG = RA * RB * RC;
   constexpr int units = M / RG;
   constexpr int total = units * NL;
@@ -207,7 +204,6 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw, const 
 #pragma unroll
     for (int j = 0; j < RG; ++j) {
       if constexpr (FROM_SRC) v[j] = src(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j));
-      else if constexpr (!std::is_same<Mul, CtBuf>::value) v[j] = mul(line, b * LP * RG + p + j * LP, base[j * step]);
       else v[j] = base[j * step];
     }
     if constexpr (FROM_SRC && ct_writes_back<Src>::value) {
@@ -278,23 +274,6 @@ template <int SIGN, int NL, int NT, int M, typename C>
 __device__ __forceinline__ void fft_dif_ct(C* buf, const C* __restrict__ tw) {
   static_assert(ct_plan(M).ok, "transform length must factor into 2, 3, 4, 5");
   ct_dif_from<SIGN, NL, NT, M, ct_plan(M).npass - 1>(buf, tw);
-}
-
-// The same with the input entries scaled as they are loaded by the first pass:
-// mul(line, m, v) for the entry at natural index m.  after_first() runs once
-// the first pass is complete in every thread (after its barrier), before the
-// remaining passes.
-template <int SIGN, int NL, int NT, int M, typename C, typename Mul, typename After>
-__device__ __forceinline__ void fft_dif_ct_mul(C* buf, const C* __restrict__ tw, const Mul& mul,
-                                               const After& after_first) {
-  constexpr CtPlan P = ct_plan(M);
-  static_assert(P.ok, "transform length must factor into 2, 3, 4, 5");
-  constexpr int I = P.npass - 1;
-  ct_pass<SIGN, false, NL, NT, M, P.lp[I], P.ra[I], P.rb[I], P.rc[I], C, CtBuf, CtBuf, Mul>(buf, tw, CtBuf(),
-                                                                                          CtBuf(), mul);
-  __syncthreads();
-  after_first();
-  ct_dif_from<SIGN, NL, NT, M, I - 1>(buf, tw);
 }
 
 // Inverse transform of each line (decimation in time, input from src in the

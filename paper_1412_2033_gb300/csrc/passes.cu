@@ -13,6 +13,7 @@
 //                     ENERGY: accumulate the Gram sums
 //                             (1/|M|) sum_m A_M(x_m) v_i(x_m).v_j(x_m).
 //                   Two real lines share one complex transform (z = u + i v).
+#include <algorithm>
 #include <cmath>
 
 #include "ghb_internal.cuh"
@@ -77,12 +78,37 @@ bool use_ct(const FftPlan& pl, bool tuned_on) {
   return sizeof(T) == 8 || tuned_on;
 }
 
+// Columns per CTA of a runtime-plan column pass over `outer` x `inner` lines:
+// the widest tile (coalesced rows of up to 16 entries) whose CTAs still fill
+// the device three times over; operands too narrow for that take the tile
+// with the most CTAs.  Wide operands (the axis-1 pass in 3-D) get wide tiles,
+// narrow ones (2-D operands of small N) narrow ones.
+int auto_tile(int M, int64_t outer, int64_t inner, int elem_bytes) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 152;
+  }
+  int fallback = 0;
+  for (int tw : {16, 8, 4, 2, 1}) {
+    const size_t smem = col_smem_bytes(M, tw, elem_bytes);
+    if (smem > 220 * 1024) continue;
+    const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (227 * 1024) / static_cast<int64_t>(smem)));
+    const int64_t ctas = outer * ((inner + tw - 1) / tw);
+    if (ctas >= 3 * per_sm * sms) return tw;
+    fallback = tw;   // the narrowest fitting tile: the most CTAs
+  }
+  return fallback > 0 ? fallback : 1;
+}
+
 template <typename T>
 ghb_status launch_col(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   using C = typename CT<T>::type;
   if (use_ct<T>(pl, pl.ct_col != 0)) return launch_col_ct<T>(sign, mode, a, pl, s);
-  const int tuned = pl.tile[sizeof(T) == 4 ? 1 : 0];
-  const int TW = tuned > 0 ? tuned : col_tile_width(pl.M, sizeof(C));
+  const int forced = pl.tile[sizeof(T) == 4 ? 1 : 0];   // ghb_tune_set; 0 = by the operand
+  const int TW = forced > 0 ? forced : auto_tile(pl.M, a.outer, a.inner, sizeof(C));
   if (col_smem_bytes(pl.M, TW, sizeof(C)) > 220 * 1024) {
     set_error("transform length too large for one CTA: M=" + std::to_string(pl.M));
     return GHB_ERR_INVALID;

@@ -4,17 +4,24 @@
 //   cap32, cap64  largest radix product of a register-blocked pass of the
 //                 runtime-plan transform (FP32, FP64): fewer passes against
 //                 more registers per thread;
-//   tile32/64     columns per CTA of the column passes;
 //   rows32        rows per CTA of the FP32 2-D operator's last-axis pass;
 //   ct_col/ct_row size-specialised FP32 kernels (where compiled) or the
 //                 runtime-plan ones.
-// How: on the first plan for M in the process, a square 2-D operand with the
-// largest odd N that M serves is allocated and every candidate is timed with
-// CUDA events on a private stream (1 untimed + 2 timed launches; the inverse
-// and forward column passes and the last-axis pass separately); the fastest
-// runtime-plan grouping by the sum of the three, then the specialised kernels
-// where they beat it.  Results stay for the life of the process.
+// The columns per CTA of the column passes (tile32/64) depend on the operand,
+// not on M alone (a 3-D axis-1 pass has ~M times the columns of a 2-D one), so
+// they are chosen at launch from the operand's shape (auto_tile) and are not
+// tuned; ghb_tune_set can still force them.
+// How: on the first plan for M in the process, a 2-D operand with the largest
+// odd N that M serves is allocated -- at least 2^20 double-grid entries per
+// component, widened with more columns and rows where N x N is smaller, so
+// that the timed launches are long enough to compare -- and every candidate is
+// timed with CUDA events on a private stream (1 untimed + 3 timed launches;
+// the inverse and forward column passes and the last-axis pass separately);
+// the fastest runtime-plan grouping by the sum of the three, then the
+// specialised kernels where they beat it.  Results stay for the life of the
+// process.
 // GHB_AUTOTUNE=0 in the environment keeps the size rules instead.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -59,10 +66,6 @@ void write_tune(const Tune& t, FftPlan& p) {
   p.ct_row = ct ? t.ct_row : 0;
 }
 
-bool tile_fits(int M, int tile, int elem_bytes, int h) {
-  return col_smem_bytes(M, tile, elem_bytes) <= 220 * 1024 && (tile == 1 || tile <= h);
-}
-
 struct Timer {
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -77,7 +80,7 @@ struct Timer {
     if (e1) cudaEventDestroy(e1);
     if (s) cudaStreamDestroy(s);
   }
-  // mean milliseconds of one launch of fn (1 untimed, 2 timed)
+  // mean milliseconds of one launch of fn (1 untimed, 3 timed)
   template <typename F>
   ghb_status time(F&& fn, float* ms) {
     {
@@ -85,7 +88,7 @@ struct Timer {
       if (st != GHB_OK) return st;
     }
     GHB_CUDA_TRY(cudaEventRecord(e0, s));
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
       const ghb_status st = fn();
       if (st != GHB_OK) return st;
     }
@@ -93,7 +96,7 @@ struct Timer {
     GHB_CUDA_TRY(cudaEventSynchronize(e1));
     float t = 0;
     GHB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-    *ms = t / 2;
+    *ms = t / 3;
     return GHB_OK;
   }
 };
@@ -158,7 +161,13 @@ ghb_status tune_length(int M, Tune* out) {
   struct {
     void* p[6];
   } b;
-  const size_t nx = 2ull * N * h, nt = 2ull * M * h, ng = static_cast<size_t>(M) * M;
+  // columns of the column passes and rows of the last-axis pass: M and h at
+  // least, 2^22 / M where that is more (cols x M >= rows x h always holds, so
+  // the last-axis pass's operand fits in the column passes' output)
+  constexpr int64_t kTarget = int64_t(1) << 20;
+  const int64_t cols = std::max<int64_t>(h, (kTarget + M - 1) / M);
+  const int64_t rows = std::max<int64_t>(M, (kTarget + M - 1) / M);
+  const size_t nx = 2ull * N * cols, nt = 2ull * M * cols, ng = static_cast<size_t>(rows) * M;
   const size_t sz[6] = {nx * sizeof(float2), nt * sizeof(float2), ng * sizeof(float),
                         nx * sizeof(double2), nt * sizeof(double2), ng * sizeof(double)};
   for (int i = 0; i < 6; ++i) TUNE_TRY(scratch(i, sz[i], &b.p[i]));
@@ -176,7 +185,7 @@ ghb_status tune_length(int M, Tune* out) {
     inv.in = X;
     inv.out = T1;
     inv.outer = 2;
-    inv.inner = h;
+    inv.inner = cols;
     inv.Lin = N;
     inv.Lout = M;
     fwd = inv;
@@ -188,13 +197,13 @@ ghb_status tune_length(int M, Tune* out) {
     row.t[0] = T1;
     row.nfields = 1;
     row.ncomp = 2;
-    row.rows = M;
+    row.rows = rows;
     row.H = h;
-    row.comp_stride = static_cast<int64_t>(M) * h;
+    row.comp_stride = rows * h;
     row.a = b.p[f32 ? 2 : 5];
   };
 
-  // FP32: runtime-plan grouping, tiles and rows, then the specialised kernels
+  // FP32: runtime-plan grouping and rows, then the specialised kernels
   {
     ColArgs inv, fwd;
     RowArgs row;
@@ -205,17 +214,13 @@ ghb_status tune_length(int M, Tune* out) {
       group_passes(p, 1, cap);
       p.ct_col = p.ct_row = 0;
       float col_best = 1e30f, row_best = 1e30f;
-      int tile_best = 0, rows_best = 0;
-      for (int tile : {1, 2, 4, 8, 16}) {
-        if (!tile_fits(M, tile, 8, h)) continue;
-        p.tile[1] = tile;
+      int rows_best = 0;
+      {
+        p.tile[1] = 0;
         float ti = 0, tf = 0;
         TUNE_TRY(tm.time([&] { return launch_col<float>(+1, COL_PLAIN, inv, p, tm.s); }, &ti));
         TUNE_TRY(tm.time([&] { return launch_col<float>(-1, COL_PLAIN, fwd, p, tm.s); }, &tf));
-        if (ti + tf < col_best) {
-          col_best = ti + tf;
-          tile_best = tile;
-        }
+        col_best = ti + tf;
       }
       for (int rows : {1, 2}) {
         p.rows32 = rows;
@@ -231,7 +236,7 @@ ghb_status tune_length(int M, Tune* out) {
         best_col_generic = col_best;
         best_row_generic = row_best;
         best.cap32 = cap;
-        best.tile32 = tile_best;
+        best.tile32 = 0;
         best.rows32 = rows_best;
       }
     }
@@ -255,7 +260,7 @@ ghb_status tune_length(int M, Tune* out) {
       }
     }
   }
-  // FP64: grouping and tiles (the last-axis pass at one row per CTA)
+  // FP64: grouping (the last-axis pass at one row per CTA)
   {
     ColArgs inv, fwd;
     RowArgs row;
@@ -265,24 +270,19 @@ ghb_status tune_length(int M, Tune* out) {
       FftPlan p = ph.plan;
       group_passes(p, 0, cap);
       float col_best = 1e30f;
-      int tile_best = 0;
-      for (int tile : {1, 2, 4, 8, 16}) {
-        if (!tile_fits(M, tile, 16, h)) continue;
-        p.tile[0] = tile;
+      {
+        p.tile[0] = 0;
         float ti = 0, tf = 0;
         TUNE_TRY(tm.time([&] { return launch_col<double>(+1, COL_PLAIN, inv, p, tm.s); }, &ti));
         TUNE_TRY(tm.time([&] { return launch_col<double>(-1, COL_PLAIN, fwd, p, tm.s); }, &tf));
-        if (ti + tf < col_best) {
-          col_best = ti + tf;
-          tile_best = tile;
-        }
+        col_best = ti + tf;
       }
       float tr = 0;
       TUNE_TRY(tm.time([&] { return launch_row<double>(ROW_MATVEC, row, p, tm.s); }, &tr));
       if (col_best + tr < best_total) {
         best_total = col_best + tr;
         best.cap64 = cap;
-        best.tile64 = tile_best;
+        best.tile64 = 0;
       }
     }
   }
