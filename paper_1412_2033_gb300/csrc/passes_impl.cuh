@@ -519,6 +519,21 @@ __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, in
 
 constexpr int kRowThreads = 256;
 
+// The size-specialised FP32 last-axis kernels read A_M from global memory in
+// their fused pass (coalesced: a warp's threads hold consecutive entries)
+// instead of staging it, which frees shared memory for a fourth CTA per SM,
+// and run 192 threads per CTA (a radix-27 pass at M = 4374 has 162
+// butterflies per line).  At M = 4374: 173 us per launch against 184 us with
+// the staged A_M and 256 threads.
+template <typename T, int MCT>
+__host__ __device__ constexpr bool row_streams_multiplier() {
+  return MCT != 0 && sizeof(T) == 4;
+}
+template <typename T, int MCT>
+__host__ __device__ constexpr int row_threads() {
+  return row_streams_multiplier<T, MCT>() ? 192 : kRowThreads;
+}
+
 // FP32: at most 85 registers so that three CTAs share an SM (measured 19 %
 // faster at M = 4374 than two CTAs of 128 registers).
 // Operator pass with staged inputs (MATVEC only; used when the staging fits
@@ -530,7 +545,9 @@ constexpr int kRowThreads = 256;
 //   smem = [ transform buffer | staged half spectra [2 NL][H] | staged A_M rows [rows][M] ]
 //
 // Copy groups in flight per thread: at the multiply, {A_M(g), spectra(g+1)};
-// wait_group 1 therefore waits for A_M(g) alone.
+// wait_group 1 therefore waits for A_M(g) alone.  Kernels that stream A_M
+// (row_streams_multiplier) have no A_M area and commit empty A_M groups, so the
+// count is the same.
 template <typename T, int NL>
 __host__ __device__ inline size_t row_staged_smem(int M, int H, int rows_per_cta) {
   using C = typename CT<T>::type;
@@ -578,6 +595,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     }
   };
   auto issue_multiplier = [&](int64_t grp) {
+    if constexpr (row_streams_multiplier<T, MCT>()) return;   // read in the fused pass instead
     for (int r = 0; r < rows_per_cta; ++r) {
       const int64_t row = grp * rows_per_cta + r;
       if (row >= a.rows) break;
@@ -613,8 +631,14 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
       };
       // multiply by A_M between the transforms, in registers
       auto mul = [&](int j, int m, C z) -> C {
-        const T a0 = ld[2 * j].valid ? sa[((2 * j) / per_row) * M + m] : T(0);
-        const T a1 = ld[2 * j + 1].valid ? sa[((2 * j + 1) / per_row) * M + m] : T(0);
+        T a0 = T(0), a1 = T(0);
+        if constexpr (row_streams_multiplier<T, MCT>()) {
+          if (ld[2 * j].valid) a0 = __ldg(&am[ld[2 * j].row * M + m]);
+          if (ld[2 * j + 1].valid) a1 = __ldg(&am[ld[2 * j + 1].row * M + m]);
+        } else {
+          if (ld[2 * j].valid) a0 = sa[((2 * j) / per_row) * M + m];
+          if (ld[2 * j + 1].valid) a1 = sa[((2 * j + 1) / per_row) * M + m];
+        }
         return mk(a0 * z.x, a1 * z.y);
       };
       auto after_first = [&]() {   // the staged spectra are read: stage the next group's
@@ -629,7 +653,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
         if (grp + nb < groups) issue_multiplier(grp + nb);
         cp_async_commit();
       };
-      ct_inverse_scale_forward<+1, -1, NL, kRowThreads, MCT>(buf, tw, src, mul, after_first, before_fused,
+      ct_inverse_scale_forward<+1, -1, NL, row_threads<T, MCT>(), MCT>(buf, tw, src, mul, after_first, before_fused,
                                                              after_fused);   // ends with a barrier
     } else {
     for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
@@ -686,7 +710,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
 }
 
 template <typename T, int NL, int MCT = 0>
-__global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(row_threads<T, MCT>(), sizeof(T) == 4 ? (row_streams_multiplier<T, MCT>() ? 4 : 3) : 1)
     row_kernel_staged(RowArgs a, FftPlan pl, int rows_per_cta) {
   row_matvec_staged<T, NL, MCT>(a, pl, rows_per_cta, blockIdx.x, gridDim.x);
 }
@@ -738,7 +762,8 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
   }
   const int64_t groups = (a.rows + rows_per_cta - 1) / rows_per_cta;
   if constexpr (MODE == ROW_MATVEC) {
-    const size_t ssmem = row_staged_smem<T, NL>(pl.M, a.H, rows_per_cta);
+    const size_t ssmem =
+        row_staged_smem<T, NL>(pl.M, a.H, row_streams_multiplier<T, MCT>() ? 0 : rows_per_cta);
     if (ssmem <= 200 * 1024) {
       // persistent grid: as many CTAs as fit on the device at once
       static int per_sm = 0, sms = 0;
@@ -747,7 +772,7 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
         GHB_CUDA_TRY(cudaFuncSetAttribute(row_kernel_staged<T, NL, MCT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         GHB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_kernel_staged<T, NL, MCT>,
-                                                                   kRowThreads, ssmem));
+                                                                   row_threads<T, MCT>(), ssmem));
         int dev = 0;
         GHB_CUDA_TRY(cudaGetDevice(&dev));
         GHB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -756,7 +781,8 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
       int64_t grid = static_cast<int64_t>(per_sm > 0 ? per_sm : 1) * sms;
       if (grid > groups) grid = groups;
       if (grid < 1) grid = 1;
-      row_kernel_staged<T, NL, MCT><<<static_cast<unsigned>(grid), kRowThreads, ssmem, s>>>(a, pl, rows_per_cta);
+      row_kernel_staged<T, NL, MCT><<<static_cast<unsigned>(grid), row_threads<T, MCT>(), ssmem, s>>>(a, pl,
+                                                                                              rows_per_cta);
       GHB_CUDA_TRY(cudaGetLastError());
       return GHB_OK;
     }
