@@ -349,9 +349,12 @@ ghb_status build_coeffs(ghb_ctx* c, double a0, const ghb_phase* phases, int n) {
       GHB_CUDA_TRY(cudaMemcpy(c->d_incs + kind * c->incs_cap, h.data(), sizeof(Incl) * n,
                               cudaMemcpyHostToDevice));
     }
-    PROF(c, PK_COEFF, false, launch_coeff_table(c->tab[kind], g, c->d_incs + kind * c->incs_cap, n, a0v, c->stream));
-    TRY(grids_from_table(c, kind));
   }
+  // both tables in one pass (shared shape factors and phases)
+  PROF(c, PK_COEFF, false,
+       launch_coeff_tables(c->tab[0], c->tab[1], g, c->d_incs, c->d_incs + c->incs_cap, n, a0, 1.0 / a0,
+                           c->stream));
+  for (int kind = 0; kind < 2; ++kind) TRY(grids_from_table(c, kind));
   return GHB_OK;
 }
 

@@ -313,9 +313,9 @@ ghb_status setup_coeffs(ghb_batch* b, Inst* in, const Request& rq) {
   // stream-ordered: the block was allocated on this stream (pageable source, staged before return)
   if (n > 0)
     GHB_CUDA_TRY(cudaMemcpyAsync(in->incs, h.data(), sizeof(Incl) * 2 * n, cudaMemcpyHostToDevice, b->stream));
+  // both tables in one pass (shared shape factors and phases)
+  TRYB(launch_coeff_tables(in->tab[0], in->tab[1], g, in->incs, in->incs + n, n, rq.a0, 1.0 / rq.a0, b->stream));
   for (int kind = 0; kind < 2; ++kind) {
-    const double a0v = kind == 0 ? rq.a0 : 1.0 / rq.a0;
-    TRYB(launch_coeff_table(in->tab[kind], g, in->incs + kind * n, n, a0v, b->stream));
     const int Nd = g.N[g.d - 1];
     if (g.d == 2) {
       ColArgs a{};

@@ -215,7 +215,11 @@ __device__ double shape_coeff(const Incl& in, int d, const int n[3]) {
   return (sq - q * cq) / (2.0 * kPi * kPi * rho2 * rho);
 }
 
-__global__ void coeff_kernel(double2* tab, Geometry g, const Incl* incs, int n, double a0v) {
+// tab1 (optional): the table of a second inclusion list with the same shapes
+// and centres (the coefficient 1/a beside a); each inclusion's shape factor and
+// phase are evaluated once for both.
+__global__ void coeff_kernel(double2* tab, double2* tab1, Geometry g, const Incl* incs, const Incl* incs1, int n,
+                             double a0v, double a0v1) {
   const int d = g.d;
   const int L0 = 2 * g.N[0] - 1;
   const int L1 = (d == 3) ? 2 * g.N[1] - 1 : g.N[1];
@@ -237,8 +241,9 @@ __global__ void coeff_kernel(double2* tab, Geometry g, const Incl* incs, int n, 
       nv[2] = static_cast<int>(rem - i1 * Ld);
     }
     (void)L0;
-    double re = (nv[0] == 0 && nv[1] == 0 && nv[2] == 0) ? a0v : 0.0;
-    double im = 0.0;
+    const bool origin = nv[0] == 0 && nv[1] == 0 && nv[2] == 0;
+    double re = origin ? a0v : 0.0, im = 0.0;
+    double re1 = origin ? a0v1 : 0.0, im1 = 0.0;
     for (int i = 0; i < n; ++i) {
       const Incl in = incs[i];
       // exp(-2 pi i n.x_i): reduce n.x_i to [-1/2, 1/2] before the sincos
@@ -247,11 +252,18 @@ __global__ void coeff_kernel(double2* tab, Geometry g, const Incl* incs, int n, 
       t -= rint(t);
       double s, c;
       sincospi(2.0 * t, &s, &c);
-      const double f = in.dv * shape_coeff(in, d, nv);
+      const double sh = shape_coeff(in, d, nv);
+      const double f = in.dv * sh;
       re += f * c;
       im -= f * s;
+      if (tab1 != nullptr) {
+        const double f1 = incs1[i].dv * sh;
+        re1 += f1 * c;
+        im1 -= f1 * s;
+      }
     }
     tab[e] = make_double2(re, im);
+    if (tab1 != nullptr) tab1[e] = make_double2(re1, im1);
   }
 }
 
@@ -579,9 +591,9 @@ __global__ void add_constant_kernel(double2* v, const double2* e, FieldGeom fg, 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-ghb_status launch_coeff_table(double2* tab, const Geometry& g, const Incl* incs, int n, double a0v,
-                              cudaStream_t s) {
-  coeff_kernel<<<field_grid(g.table), kFieldThreads, 0, s>>>(tab, g, incs, n, a0v);
+ghb_status launch_coeff_tables(double2* tab0, double2* tab1, const Geometry& g, const Incl* incs0,
+                               const Incl* incs1, int n, double a0v0, double a0v1, cudaStream_t s) {
+  coeff_kernel<<<field_grid(g.table), kFieldThreads, 0, s>>>(tab0, tab1, g, incs0, incs1, n, a0v0, a0v1);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }

@@ -217,8 +217,11 @@ inline FieldGeom make_field_geom(int d, int N0, int N1, int N2, int h, int64_t P
   return f;
 }
 
-ghb_status launch_coeff_table(double2* tab, const Geometry& g, const Incl* incs, int n, double a0v,
-                              cudaStream_t s);
+// Coefficient tables on Z_{2N-1} (eq. inclcomp_formula) of the inclusion lists
+// incs0 and, when tab1 is not null, incs1 (same shapes and centres, other jumps:
+// the coefficient 1/a beside a), each list's background value a0v0 / a0v1.
+ghb_status launch_coeff_tables(double2* tab0, double2* tab1, const Geometry& g, const Incl* incs0,
+                               const Incl* incs1, int n, double a0v0, double a0v1, cudaStream_t s);
 template <typename T>
 ghb_status launch_rhs(void* b, const double2* tab, const Geometry& g, const double* E, int kind,
                       cudaStream_t s);
