@@ -369,17 +369,26 @@ def run_ours(args, world, rank, local):
         ccoarse = g.Context.from_microstructure(dict(m, N=[Nc, Nc]), precision="mixed", tol=1e-10)
         for s_ in (cfine, ccoarse):
             s_.set_stream(stream)
+
+        def warm_path():
+            fc, icoarse, _, _ = ccoarse.solve_ex(E)
+            ec = fc.clone()
+            ec[0, (Nc - 1) // 2, 0] -= E[0]
+            x0 = g.prolong(ec, [args.N, args.N])
+            _, iwarm, ewarm, _ = cfine.solve_ex(E, x0=x0, energies=True)
+            return icoarse, iwarm, ewarm
+
+        # one untimed pass of both paths first (first launches of their kernels,
+        # which the first process after a build loads from the library file)
+        cfine.solve_ex(E, energies=True)
+        warm_path()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, icold, ecold, _ = cfine.solve_ex(E, energies=True)
         torch.cuda.synchronize()
         t_cold = time.perf_counter() - t0
         t0 = time.perf_counter()
-        fc, icoarse, _, _ = ccoarse.solve_ex(E)
-        ec = fc.clone()
-        ec[0, (Nc - 1) // 2, 0] -= E[0]
-        x0 = g.prolong(ec, [args.N, args.N])
-        _, iwarm, ewarm, _ = cfine.solve_ex(E, x0=x0, energies=True)
+        icoarse, iwarm, ewarm = warm_path()
         torch.cuda.synchronize()
         t_warm = time.perf_counter() - t0
         warm = {"coarse_N": Nc, "cold": {"s": t_cold, "inner_iters": icold["iters"], "start_bound": ecold[0],
