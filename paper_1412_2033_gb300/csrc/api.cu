@@ -1551,25 +1551,23 @@ ghb_status ghb_prolong(int d, const int* Nc, const void* xc_dev, const int* Nf, 
     set_error("ghb_prolong: d must be 2 or 3 and no pointer may be NULL");
     return GHB_ERR_INVALID;
   }
-  FieldGeom fc{d, {1, 1, 1}, 0, 0}, ff{d, {1, 1, 1}, 0, 0};
+  int nc[3] = {1, 1, 1}, nf[3] = {1, 1, 1};
   for (int a = 0; a < d; ++a) {
     if (Nc[a] < 1 || Nc[a] % 2 == 0 || Nf[a] < Nc[a] || Nf[a] % 2 == 0) {
       set_error("ghb_prolong: orders must be odd with N_fine >= N_coarse in every direction");
       return GHB_ERR_INVALID;
     }
-    fc.N[a] = Nc[a];
-    ff.N[a] = Nf[a];
+    nc[a] = Nc[a];
+    nf[a] = Nf[a];
   }
-  fc.h = (Nc[d - 1] + 1) / 2;
-  ff.h = (Nf[d - 1] + 1) / 2;
-  fc.P = fc.h;
-  ff.P = ff.h;
+  const int hc = (nc[d - 1] + 1) / 2, hf = (nf[d - 1] + 1) / 2;
+  int64_t Pc = hc, Pf = hf;
   for (int a = 0; a < d - 1; ++a) {
-    fc.P *= Nc[a];
-    ff.P *= Nf[a];
+    Pc *= nc[a];
+    Pf *= nf[a];
   }
-  fc = make_field_geom(d, fc.N[0], fc.N[1], fc.N[2], fc.h, fc.P);
-  ff = make_field_geom(d, ff.N[0], ff.N[1], ff.N[2], ff.h, ff.P);
+  const FieldGeom fc = make_field_geom(d, nc[0], nc[1], nc[2], hc, Pc);
+  const FieldGeom ff = make_field_geom(d, nf[0], nf[1], nf[2], hf, Pf);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY(launch_prolong(static_cast<double2*>(xf_dev), ff, static_cast<const double2*>(xc_dev), fc, s));
   GHB_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1607,7 +1605,7 @@ ghb_status ghb_bounds_gani(ghb_ctx* c, double* upper, double* lower, double* a_g
       for (int j = 0; j < d; ++j) Y[i * d + j] = 0.5 * (X[i * d + j] + X[j * d + i]);
   };
   auto inv_sym = [&](const double* X, double* Y) -> bool {
-    double S[9], L[9];
+    double S[9] = {}, L[9] = {};
     sym(X, S);
     if (!inverse_small(d, S, L)) return false;
     sym(L, Y);
