@@ -154,10 +154,26 @@ def coeff_table(mat: Material, N) -> np.ndarray:
     return coeff_at(mat, freq_grid([2 * n - 1 for n in N]))
 
 
+def _overlap_at(a: Inclusion, b: Inclusion, delta: np.ndarray, d: int) -> bool:
+    """Do the open interiors of inclusion a (centred at 0) and inclusion b
+    (centred at delta) intersect?  Touching shapes do not overlap."""
+    ra, rb = a.shape in (DISK, SPHERE), b.shape in (DISK, SPHERE)
+    if ra and rb:                                    # two balls: centre distance
+        return float(np.linalg.norm(delta)) < a.size[0] + b.size[0]
+    if not ra and not rb:                            # two boxes: every axis overlaps
+        return all(abs(delta[x]) < 0.5 * (a.size[x] + b.size[x]) for x in range(d))
+    box, ball = (b, a) if ra else (a, b)
+    off = delta if ra else -delta                    # ball centre relative to the box centre
+    gap = np.maximum(np.abs(off) - 0.5 * np.asarray(box.size[:d], dtype=np.float64), 0.0)
+    return float(np.linalg.norm(gap)) < ball.size[0]  # distance from the box to the ball centre
+
+
 def validate(mat: Material) -> None:
     """Admissibility checks: SPD values (eq. A), inclusions that do not meet
     their own periodic images (box h_a <= 1, radius <= 1/2) and do not overlap
-    each other (needed for the table of 1/a to be of the form (*))."""
+    each other or each other's periodic images (needed for the table of 1/a to
+    be of the form (*)).  Every pair is checked against the 3^d nearest images
+    of the second inclusion."""
     if not (mat.a0 > 0 and all(i.value > 0 for i in mat.inclusions)):
         raise ValueError("coefficients must be positive")
     for i in mat.inclusions:
@@ -165,13 +181,17 @@ def validate(mat: Material) -> None:
             raise ValueError("box side must be in (0, 1]")
         if i.shape in (DISK, SPHERE) and not (0 < i.size[0] <= 0.5):
             raise ValueError("radius must be in (0, 1/2]")
-    round_ = [i for i in mat.inclusions if i.shape in (DISK, SPHERE)]
-    for a in range(len(round_)):
-        for b in range(a + 1, len(round_)):
-            delta = np.asarray(round_[a].center[: mat.d]) - np.asarray(round_[b].center[: mat.d])
-            delta = delta - np.round(delta)          # torus (periodic) distance
-            if np.linalg.norm(delta) < round_[a].size[0] + round_[b].size[0]:
-                raise ValueError("inclusions overlap")
+    d = mat.d
+    shifts = np.stack(np.meshgrid(*([np.arange(-1, 2)] * d), indexing="ij"), axis=-1).reshape(-1, d)
+    incs = mat.inclusions
+    for a in range(len(incs)):
+        for b in range(a + 1, len(incs)):
+            delta = (np.asarray(incs[b].center[:d], dtype=np.float64)
+                     - np.asarray(incs[a].center[:d], dtype=np.float64))
+            delta = delta - np.round(delta)
+            for s in shifts:
+                if _overlap_at(incs[a], incs[b], delta + s, d):
+                    raise ValueError("inclusions overlap")
 
 
 def material_from_dict(m: dict) -> Material:

@@ -37,6 +37,8 @@ Operators written out (each is the plain definition from the cited passage):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from .coefficients import Material, coeff_at, coeff_table, freq_grid, validate
@@ -178,6 +180,16 @@ def inner(x: np.ndarray, y: np.ndarray) -> float:
     return float(np.real(np.vdot(y, x)))
 
 
+def inner_exact(x: np.ndarray, y: np.ndarray) -> float:
+    """The same scalar product with the sum of the products Re x conj y =
+    x_re y_re + x_im y_im correctly rounded (math.fsum), so that the only
+    rounding left in an energy is that of its operands.  Used for the bound
+    energies (eq. GA_prim), whose terms cancel at high contrast."""
+    xr, xi = np.real(x).ravel(), np.imag(x).ravel()
+    yr, yi = np.real(y).ravel(), np.imag(y).ravel()
+    return math.fsum(np.concatenate((xr * yr, xi * yi)))
+
+
 def constant_field(E, N) -> np.ndarray:
     """The constant field E as coefficients on Z_N: E at k = 0, zero elsewhere."""
     d = len(N)
@@ -246,7 +258,7 @@ class Operator:
 
     def energy(self, v: np.ndarray, w: np.ndarray) -> float:
         """a(v, w) = Re sum_l conj(w(l)) . (A^full v)(l) (Lemma FD_matrix_full)."""
-        return inner(self.apply(v, project_out=False), w)
+        return inner_exact(self.apply(v, project_out=False), w)
 
 
 def cg(op: Operator, b: np.ndarray, tol: float, maxiter: int = 10000, x0=None, track_energy_E=None):
@@ -312,38 +324,61 @@ def gram(op: Operator, fields) -> np.ndarray:
     """Symmetrised Gram matrix X_ij = a(v_i, v_j) of the admissible fields v_i."""
     m = len(fields)
     Av = [op.apply(v, project_out=False) for v in fields]
-    X = np.array([[inner(Av[i], fields[j]) for j in range(m)] for i in range(m)])
+    X = np.array([[inner_exact(Av[i], fields[j]) for j in range(m)] for i in range(m)])
     return 0.5 * (X + X.T)
+
+
+def admissible(e: np.ndarray, kind: str) -> np.ndarray:
+    """The nearest admissible fluctuation: the Hermitian part (the coefficients
+    of a real trigonometric polynomial, Def. trig_pol: e(-k) = conj e(k)),
+    projected onto the range of G (Def. projection).  Exact on admissible
+    fields; applied to a computed minimiser it removes the rounding left outside
+    E_N (J_N), so that its energy is that of an admissible field (Def. Ga)."""
+    d = e.shape[0]
+    flip = e[(slice(None),) + (slice(None, None, -1),) * d]
+    return project(0.5 * (e + np.conj(flip)), kind)
 
 
 def solve_load(op: Operator, E, tol: float = 1e-10, method: str = "cg", maxiter: int = 10000):
     """Minimiser e of a(E + e, E + e) over E_N (primal) or J_N (dual) and the
-    admissible field v = E + e.  Returns (v, info)."""
+    admissible field v = E + e, with e made exactly admissible (``admissible``).
+    Returns (v, info)."""
     b = op.rhs(E)
     if method == "cg":
         e, info = cg(op, b, tol, maxiter)
     else:
         e, info = solve_dense(op, b), dict(iters=0, relres=0.0, converged=True, energies=[])
-    return constant_field(E, op.N) + e, info
+    return constant_field(E, op.N) + admissible(e, op.kind), info
+
+
+def _solve_task(args):
+    """One load of ``bounds`` (module level so that a process pool can run it)."""
+    mat, N, kind, M, op_method, E, tol, method, maxiter = args
+    op = Operator(mat, N, kind, M=M, method=op_method)
+    return solve_load(op, E, tol=tol, method=method, maxiter=maxiter)
 
 
 def bounds(mat: Material, N, M=None, tol: float = 1e-10, method: str = "cg",
-           op_method: str = "double_grid", maxiter: int = 10000):
+           op_method: str = "double_grid", maxiter: int = 10000, pool=None):
     """Guaranteed bounds of the Ga scheme (Def. Ga, Prop. struct_bounds).
 
     Returns (upper, lower, infos): upper = Gram of the d primal admissible
     fields in a(.,.), lower = inverse of the Gram of the d dual fields in
-    a^{-1}(.,.) (eq. spd_inverse_ineq).
+    a^{-1}(.,.) (eq. spd_inverse_ineq).  The 2d solves are independent; with
+    ``pool`` (an executor with ``map``) they run there, else one after another.
     """
     d = len(N)
     eye = np.eye(d)
+    tasks = [(mat, list(N), kind, M, op_method, eye[i], tol, method, maxiter)
+             for kind in (PRIMAL, DUAL) for i in range(d)]
+    solved = list(pool.map(_solve_task, tasks)) if pool is not None else [_solve_task(t) for t in tasks]
     out = {}
     infos = {}
     for kind in (PRIMAL, DUAL):
         op = Operator(mat, N, kind, M=M, method=op_method)
         fields = []
         for i in range(d):
-            v, info = solve_load(op, eye[i], tol=tol, method=method, maxiter=maxiter)
+            v, info = solved[(0 if kind == PRIMAL else d) + i]
             fields.append(v)
             infos[(kind, i)] = info
         out[kind] = gram(op, fields)

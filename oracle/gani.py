@@ -97,7 +97,7 @@ def gani_bounds(mat: Material, N, M=None, tol: float = 1e-12, maxiter: int = 100
         for i in range(d):
             b = opn.rhs(eye[i])
             e, info = G.cg(opn, b, tol, maxiter)
-            fields.append(G.constant_field(eye[i], N) + e)
+            fields.append(G.constant_field(eye[i], N) + G.admissible(e, kind))
             infos[(kind, i)] = info
         approx[kind] = G.gram(opn, fields)
         exact[kind] = G.gram(G.Operator(mat, N, kind, M=M), fields)

@@ -141,6 +141,89 @@ def test_validate_rejects_bad_inputs():
                                        C.Inclusion(C.DISK, (-0.45, 0), (0.1,), 2.0)]))
 
 
+def test_validate_overlap_every_pair():
+    """Every pair of inclusions is checked, boxes included, through the
+    periodic boundary; touching shapes are allowed (their open interiors are
+    disjoint, so the table of 1/a is still of the composite form)."""
+    B, D, S = C.BOX, C.DISK, C.SPHERE
+    bad = [
+        [C.Inclusion(B, (0.45, 0.0), (0.2, 0.2), 2.0), C.Inclusion(B, (-0.45, 0.05), (0.2, 0.2), 3.0)],
+        [C.Inclusion(B, (0.0, 0.0), (0.4, 0.4), 2.0), C.Inclusion(D, (0.3, 0.3), (0.15,), 3.0)],
+        [C.Inclusion(D, (0.3, 0.3), (0.15,), 3.0), C.Inclusion(B, (0.0, 0.0), (0.4, 0.4), 2.0)],
+        [C.Inclusion(B, (0.0, 0.45), (1.0, 0.3), 2.0), C.Inclusion(D, (0.3, -0.4), (0.1,), 3.0)],
+    ]
+    for incs in bad:
+        with pytest.raises(ValueError):
+            C.validate(C.Material(2, 1.0, incs))
+    good = [
+        [C.Inclusion(B, (0.45, 0.0), (0.2, 0.2), 2.0), C.Inclusion(B, (-0.2, 0.0), (0.2, 0.2), 3.0)],
+        [C.Inclusion(B, (0.0, 0.0), (0.4, 0.4), 2.0), C.Inclusion(D, (0.3, 0.3), (0.1,), 3.0)],
+        [C.Inclusion(B, (0.0, 0.0), (0.4, 0.4), 2.0), C.Inclusion(B, (0.4, 0.0), (0.4, 0.4), 3.0)],  # touching
+    ]
+    for incs in good:
+        C.validate(C.Material(2, 1.0, incs))
+    with pytest.raises(ValueError):   # 3-D: a sphere meeting a box through the z boundary
+        C.validate(C.Material(3, 1.0, [C.Inclusion(B, (0.0, 0.0, 0.45), (0.3, 0.3, 0.2), 2.0),
+                                       C.Inclusion(S, (0.0, 0.0, -0.35), (0.1,), 3.0)]))
+    C.validate(C.Material(3, 1.0, [C.Inclusion(B, (0.0, 0.0, 0.45), (0.3, 0.3, 0.2), 2.0),
+                                   C.Inclusion(S, (0.0, 0.0, -0.2), (0.1,), 3.0)]))
+
+
+def test_validate_overlap_against_sampled_shapes():
+    """Brute force: random pairs of boxes and disks, overlap decided by
+    sampling the two periodic characteristic functions on a 512^2 point grid;
+    pairs within two grid spacings of touching are skipped (undecidable by
+    sampling).  The validation must agree on every other pair."""
+    rng = np.random.default_rng(4)
+    n = 512
+    x = (np.arange(n) + 0.5) / n - 0.5
+    X, Y = np.meshgrid(x, x, indexing="ij")
+
+    def inside(inc, margin):
+        dx = X - inc.center[0]
+        dy = Y - inc.center[1]
+        dx -= np.round(dx)
+        dy -= np.round(dy)
+        if inc.shape == C.BOX:
+            return (np.abs(dx) < 0.5 * inc.size[0] - margin) & (np.abs(dy) < 0.5 * inc.size[1] - margin)
+        return np.hypot(dx, dy) < inc.size[0] - margin
+
+    h = 2.0 / n
+    checked = 0
+    for _ in range(300):
+        incs = []
+        for _k in range(2):
+            c = tuple(rng.uniform(-0.5, 0.5, 2))
+            if rng.uniform() < 0.5:
+                incs.append(C.Inclusion(C.BOX, c, tuple(rng.uniform(0.05, 0.5, 2)), 2.0))
+            else:
+                incs.append(C.Inclusion(C.DISK, c, (rng.uniform(0.03, 0.25),), 2.0))
+        surely = np.any(inside(incs[0], 0.0) & inside(incs[1], h))          # a point well inside both
+        maybe = np.any(inside(incs[0], -h) & inside(incs[1], -h))           # grown shapes meet
+        if surely == maybe:
+            try:
+                C.validate(C.Material(2, 1.0, incs))
+                rejected = False
+            except ValueError:
+                rejected = True
+            assert rejected == bool(surely), incs
+            checked += 1
+    assert checked > 200
+
+
+def test_inner_exact_sums_without_cancellation_loss():
+    """The bound energies' scalar product: products rounded once, their sum
+    exact up to the last rounding (Shewchuk's summation, math.fsum)."""
+    from oracle import galerkin as G
+    x = np.array([1e16, 1.0, -1e16, 3.0 + 2.0j])
+    y = np.array([1.0, 1.0, 1.0, 1.0 - 1.0j])
+    assert G.inner_exact(x, y) == 1.0 + 3.0 - 2.0
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal(1000) + 1j * rng.standard_normal(1000)
+    b = rng.standard_normal(1000) + 1j * rng.standard_normal(1000)
+    assert abs(G.inner_exact(a, b) - G.inner(a, b)) < 1e-12 * np.abs(a).sum()
+
+
 def test_large_argument_accuracy_against_mpmath():
     """High frequencies (N up to 2187 reaches |n| ~ 3000): the sinc factor, the
     disk's J1 term and the shift phase against 30-digit mpmath evaluations."""
