@@ -59,13 +59,30 @@ def parse():
                     help="GaNi a-posteriori bound pairs timed on the same workload (0 = skip)")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="instances of the batched workload (0 = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
-                    help="arrival window of the served workload (0 = skip)")
-    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--batch-sample", type=int, default=16,
+                    help="randomly drawn instances on which the batched and the FP64 single-solve arms "
+                         "are both timed")
+    ap.add_argument("--d3-N", type=str, default="33,65,129",
+                    help="orders of the d = 3 sphere / cube legs (comma list; empty = skip)")
+    ap.add_argument("--d3-fp64-max-N", type=int, default=129,
+                    help="largest d = 3 order also timed on the plain FP64 path")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="measured arrival window of the sustained served run (0 = skip the served leg)")
+    ap.add_argument("--serve-warmup", type=float, default=2.0,
+                    help="arrival window before the measured one (its requests are not counted)")
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="sustained arrival rate as a fraction of the measured service capacity")
+    ap.add_argument("--serve-probe", type=int, default=48,
+                    help="requests of the closed-loop capacity probe (mixed; a quarter of it for FP64)")
+    ap.add_argument("--serve-overload-rate", type=float, default=200.0,
+                    help="arrival rate of the short overload run (0 = skip)")
+    ap.add_argument("--serve-overload-seconds", type=float, default=2.0)
     ap.add_argument("--serve-drain", type=float, default=30.0,
-                    help="seconds after the last arrival before the served leg stops waiting")
+                    help="seconds after the last arrival before a served run stops waiting")
     ap.add_argument("--serve-slots", type=int, default=64,
                     help="requests the server solves at once (more wait in its queue)")
+    ap.add_argument("--serve-fp64-seconds", type=float, default=20.0,
+                    help="measured arrival window of the plain FP64 served run (0 = skip)")
     ap.add_argument("--matvec-only", choices=["f32", "f64"], default=None,
                     help="only apply the operator (warmup + steps times) at the workload size; "
                          "prints the mean time per application (used for ncu captures)")
@@ -212,7 +229,7 @@ def oracle_matvec_times(N, M, reps):
 # 2 primal + 2 dual CG solves (iterations measured on the FP64 GPU path, same
 # algorithm and tolerance) plus one application per admissible field for the
 # Gram energies.  Printed by the ours arm as "fp64.matvecs_per_pair".
-FP64_MATVECS_PER_PAIR = {2187: None}
+FP64_MATVECS_PER_PAIR = {2187: 350}
 
 
 def run_reference(args, world, rank):
@@ -228,14 +245,18 @@ def run_reference(args, world, rank):
     t = sum(res["matvec_s"]) / len(res["matvec_s"])
     mv = mv_pair if mv_pair else 4 * 100 + 4
     value = 1.0 / (t * mv)
+    extrapolated = (f"extrapolated: {reps} oracle operator application(s) timed, x {mv} applications of one "
+                    f"FP64 bound pair (the count the FP64 GPU path measures at this workload)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": reps, "warmup": args.warmup, "ms_per_step": 1e3 * t * mv, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(N), "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": f"{reps} oracle operator applications at N={N}, M={M} "
-                                   f"(mean {t:.2f} s each), x {mv} applications per bound pair"},
+                                   f"(mean {t:.2f} s each), x {mv} applications per bound pair",
+                         "extrapolation": extrapolated},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -334,6 +355,7 @@ def run_ours(args, world, rank, local):
         err_u = float(np.abs(U - U64).max() / np.abs(U64).max())
         err_l = float(np.abs(L - L64).max() / np.abs(L64).max())
         fp64 = {"bound_pairs_per_s": 1.0 / t64, "s_per_pair": t64, "matvecs_per_pair": mv64,
+                "grid_pt_iter_per_s": grid_pts * mv64 / t64,
                 "mixed_speedup": value / world / (1.0 / t64), "rel_err_upper": err_u, "rel_err_lower": err_l,
                 "upper": U64.tolist(), "lower": L64.tolist()}
         c64.close()
@@ -458,6 +480,7 @@ def run_ours(args, world, rank, local):
         e2e_ts.append(time.perf_counter() - t0)
     e2e_t = allmax(world, statistics.median(e2e_ts)) if e2e_ts else float("nan")
 
+    d3 = run_d3(args, g, stream) if args.d3_N.strip() else None
     batched = run_batched(args, g) if args.batch_count > 0 else None
     served = run_served(args, g) if args.serve_seconds > 0 else None
 
@@ -467,13 +490,37 @@ def run_ours(args, world, rank, local):
             res = oracle_matvec_times(args.N, ctx.M[0], 1)
             t = res["matvec_s"][0]
             mvp = fp64["matvecs_per_pair"] if fp64 else 4 * 100 + 4
-            cpu = {"value": 1.0 / (t * mvp), "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": 1.0 / (t * mvp), "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                   "kind": "oracle",
                    "sample": f"1 oracle operator application at N={args.N}, M={ctx.M[0]} ({t:.1f} s, "
-                             f"set-up {res['setup_s']:.1f} s) x {mvp} applications per FP64 bound pair"}
+                             f"set-up {res['setup_s']:.1f} s) x {mvp} applications per FP64 bound pair "
+                             f"(extrapolated from the one timed application)"}
         except Exception as ex:  # noqa: BLE001
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"}
 
     if rank == 0:
+        summary = {"mixed_pairs_per_s": value / world,
+                   "mixed_grid_pt_iter_per_s": gpi / world}
+        if fp64:
+            summary.update({"fp64_pairs_per_s": fp64["bound_pairs_per_s"],
+                            "fp64_grid_pt_iter_per_s": fp64["grid_pt_iter_per_s"],
+                            "mixed_speedup": fp64["mixed_speedup"],
+                            "rel_err_mixed_vs_fp64": max(fp64["rel_err_upper"], fp64["rel_err_lower"])})
+        if d3:
+            summary["d3"] = {f'{c["shape"]}{c["N"]}': {k: c.get(k) for k in ("mixed_pairs_per_s", "fp64_pairs_per_s",
+                                                                              "mixed_speedup", "rel_err_upper")}
+                             for c in d3["cases"]}
+        if batched:
+            summary["batched"] = {"pairs_per_s": batched["bound_pairs_per_s"],
+                                  "sample_speedup_vs_fp64_single": batched["sample"]["speedup_vs_fp64_single"]}
+        if served:
+            summary["served"] = {arm: {"rate": served[arm]["rate_req_per_s"],
+                                       "pairs_per_s": served[arm]["bound_pairs_per_s"],
+                                       "p50_ms": served[arm]["latency_ms"]["p50"],
+                                       "p99_ms": served[arm]["latency_ms"]["p99"]}
+                                 for arm in ("mixed", "fp64", "overload") if arm in served}
+        top = dict(list(kernels.items())[:8])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
@@ -483,20 +530,8 @@ def run_ours(args, world, rank, local):
                        "precision": "mixed: FP32 inner CG, FP64 residual correction, FP64 projection and Gram",
                        "tol": 1e-10, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (per-step working set ~1.5 GB)"},
-            "grid_pt_iter_per_s": gpi,
-            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
-                                                                            int(0.99 * len(lat_ms)))]},
-            "bounds": {"upper": U.tolist(), "lower": L.tolist()},
-            "solves": infos,
-            "fp64": fp64,
-            "gani": gani,
-            "warm_start": warm,
-            "reduced": reduced,
-            "image": image,
-            "batched": batched,
-            "served": served,
+            "summary": summary,
             "roofline": roof,
-            "kernels": kernels,
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": {"value": pairs / e2e_t / args.steps * args.steps if e2e_ts else None, "unit": UNIT,
@@ -504,6 +539,19 @@ def run_ours(args, world, rank, local):
                     "what": "ghb_create (device set-up from the host inclusion list) + ghb_bounds "
                             "(results to host) + ghb_destroy, host wall clock"},
             "cpu_baseline": cpu,
+            "grid_pt_iter_per_s": gpi,
+            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                            int(0.99 * len(lat_ms)))]},
+            "fp64": fp64,
+            "d3": d3,
+            "batched": batched,
+            "served": served,
+            "gani": gani,
+            "warm_start": warm,
+            "reduced": reduced,
+            "image": image,
+            "bounds": {"upper": U.tolist(), "lower": L.tolist()},
+            "kernels_top": top,
         }
         if line["e2e"]["value"] is not None:
             line["e2e"]["value"] = world / e2e_t
@@ -511,74 +559,118 @@ def run_ours(args, world, rank, local):
     ctx.close()
 
 
+def _auto_M(N):
+    """The library's automatic double grid: the smallest M >= 2N - 1 whose
+    prime factors are 2, 3 and 5."""
+    M = 2 * N - 1
+    while True:
+        m = M
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return M
+        M += 1
+
+
+def _grid_pt_iters(M, infos, d):
+    """grid-pt.iter of one bound pair: |M| x operator applications (FP32 and
+    FP64 iterations and corrections, plus one application per admissible field
+    for the Gram energies)."""
+    import numpy as np
+    mv = sum(i["matvecs_fp32"] + i["matvecs_fp64"] for i in infos) + 2 * d
+    return float(np.prod(M)) * mv
+
+
 def run_batched(args, g):
     """The 512-instance workload: K ~ U{1..20} disks of radius U(0.03, 0.12),
     contrast log-uniform in [2, 1e4], N odd uniform in 31..255; all instances
     solved together by the batch engine (one launch per kernel and CG
-    iteration over every active solve).  Compared with the plain FP64
-    single-solve path on a sample of the same instances."""
+    iteration over every active solve).  The batched and the plain FP64
+    single-solve arms are also both timed on one randomly drawn sample of the
+    same instances, and both report grid-pt.iter/s."""
     import numpy as np
     import torch
 
     import workloads as W
     inst = W.disk_batch(args.batch_count)
-    b = g.Batch()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for m in inst:
-        b.submit(m)
-    b.run(iterations=8)
-    t = time.perf_counter() - t0
-    res = {r["id"]: r for r in b.results()}
-    st = b.stats()
-    b.close()
-    ok = sum(1 for r in res.values() if r["status"] == 0)
-    iters = [sum(i["iters"] for i in r["infos"]) for r in res.values()]
-    # plain FP64 single-solve GPU path on a sample
-    sample = inst[: min(8, len(inst))]
+
+    def batched_run(items):
+        b = g.Batch()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [b.submit(m) for m in items]
+        b.run(iterations=8)
+        t = time.perf_counter() - t0
+        res = {r["id"]: r for r in b.results()}
+        st = b.stats()
+        b.close()
+        return t, [res[i] for i in ids], st
+
+    t, res, st = batched_run(inst)
+    ok = sum(1 for r in res if r["status"] == 0)
+    iters = [sum(i["iters"] for i in r["infos"]) for r in res]
+    # the same randomly drawn sample through both arms
+    rng = np.random.default_rng(20141206)
+    pick = sorted(rng.choice(len(inst), size=min(args.batch_sample, len(inst)), replace=False).tolist())
+    sample = [inst[k] for k in pick]
+    tb, resb, _ = batched_run(sample)
+    gpi_b = 0.0
+    for m, r in zip(sample, resb):
+        M = [_auto_M(n) for n in m["N"]]
+        gpi_b += _grid_pt_iters(M, r["infos"], m["d"])
     errs = []
     t64 = 0.0
-    ids = sorted(res)
-    for k, m in enumerate(sample):
+    gpi_64 = 0.0
+    for m, r in zip(sample, resb):
         c = g.Context.from_microstructure(m, precision="fp64", tol=1e-10)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        U, L, _, _ = c.bounds()
+        U, L, inf64, _ = c.bounds()
         torch.cuda.synchronize()
         t64 += time.perf_counter() - t1
+        gpi_64 += _grid_pt_iters(c.M, inf64, m["d"])
         c.close()
-        r = res[ids[k]]
         errs.append(max(float(np.abs(r["upper"] - U).max() / np.abs(U).max()),
                         float(np.abs(r["lower"] - L).max() / np.abs(L).max())))
-    fp64_rate = len(sample) / t64
     return {"workload": f"{len(inst)} seeded d2 disk instances, N odd 31..255, contrast 2..1e4",
             "bound_pairs_per_s": len(inst) / t, "seconds": t, "ok": ok,
             "cg_iterations_per_pair_mean": float(np.mean(iters)), "launches": st["launches"],
-            "fp64_single_solve_pairs_per_s": fp64_rate, "fp64_sample": len(sample),
-            "speedup_vs_fp64_single": (len(inst) / t) / fp64_rate,
-            "max_rel_err_vs_fp64_sample": max(errs) if errs else None}
+            "sample": {"instances": pick, "batched_pairs_per_s": len(sample) / tb,
+                       "batched_grid_pt_iter_per_s": gpi_b / tb,
+                       "fp64_single_solve_pairs_per_s": len(sample) / t64,
+                       "fp64_single_solve_grid_pt_iter_per_s": gpi_64 / t64,
+                       "speedup_vs_fp64_single": (len(sample) / tb) / (len(sample) / t64),
+                       "max_rel_err_vs_fp64": max(errs) if errs else None,
+                       "note": "both arms timed on the same seeded random sample of the 512 instances "
+                               "(batched: submit to results; FP64: one context per instance, bounds only)"}}
 
 
-def run_served(args, g):
-    """Poisson arrivals (rate per second) of bound requests mixing d = 2 disk
-    instances (N odd 63..1023) and d = 3 sphere instances (N odd 15..129),
-    submitted as they arrive into one batch (continuous batching).  Latency =
-    arrival -> result on the host clock."""
-    import numpy as np
-
+def _serve_stream(rate, seconds, seed):
     import workloads as W
-    stream = W.request_stream(rate=args.serve_rate, duration=args.serve_seconds)
-    b = g.Batch(max_active=args.serve_slots)
+    return W.request_stream(rate=rate, duration=seconds, seed=seed)
+
+
+def _percentiles(lat):
+    lat = sorted(lat)
+    if not lat:
+        return {"p50": None, "p99": None}
+    return {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+
+def _serve_mixed(g, stream, slots, t_measure0, t_measure1, drain):
+    """Feed (arrival, request) pairs into one batch as they arrive (continuous
+    batching).  Returns latency stats of the requests that arrived inside
+    [t_measure0, t_measure1) and the completion rate over the arrival window."""
+    b = g.Batch(max_active=slots)
     t0 = time.perf_counter()
-    arrivals = {}
-    done = {}
+    arrivals, done = {}, {}
     i = 0
-    deadline = args.serve_seconds + args.serve_drain
+    deadline = (stream[-1][0] if stream else 0.0) + drain
     while (i < len(stream) or len(done) < i) and time.perf_counter() - t0 < deadline:
         now = time.perf_counter() - t0
         while i < len(stream) and stream[i][0] <= now:
-            rid = b.submit(stream[i][1])
-            arrivals[rid] = stream[i][0]
+            arrivals[b.submit(stream[i][1])] = stream[i][0]
             i += 1
         if len(done) < i:
             b.step(iterations=4)
@@ -589,18 +681,169 @@ def run_served(args, g):
             time.sleep(0.0005)
     wall = time.perf_counter() - t0
     b.close()
-    # requests still unfinished at the cutoff count with their age at the cutoff
-    # (a lower bound on their latency), so the percentiles are not flattered
-    lat = sorted([done[k][0] - arrivals[k] for k in done] +
-                 [wall - arrivals[k] for k in arrivals if k not in done])
-    n2 = sum(1 for _, m in stream[:i] if m["d"] == 2)
-    return {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s, "
-                        f"d2 disks N 63..1023 / d3 spheres N 15..129",
-            "submitted": i, "completed": len(done), "d2": n2, "d3": i - n2, "slots": args.serve_slots,
-            "latency_note": "arrival to result; unfinished requests enter with their age at the cutoff",
-            "bound_pairs_per_s": len(done) / wall, "wall_s": wall,
-            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2] if lat else None,
-                           "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None}}
+    meas = [k for k, a in arrivals.items() if t_measure0 <= a < t_measure1]
+    # requests still unfinished at the cutoff enter with their age at the cutoff
+    lat = [(done[k][0] if k in done else wall) - arrivals[k] for k in meas]
+    fin = [done[k][0] for k in meas if k in done]
+    window = max(fin) - t_measure0 if fin else float("nan")
+    return {"submitted": len(meas), "completed": len(fin), "unfinished_at_cutoff": len(meas) - len(fin),
+            "latency_ms": _percentiles(lat), "mean_latency_ms": 1e3 * sum(lat) / len(lat) if lat else None,
+            "bound_pairs_per_s": len(fin) / window if fin else 0.0, "wall_s": wall,
+            "ok": sum(1 for k in meas if k in done and done[k][1] == 0)}
+
+
+def _serve_fp64(g, stream, t_measure0, t_measure1, drain):
+    """The plain FP64 single-solve server: requests in arrival order, one FP64
+    context at a time (create, bounds, destroy)."""
+    import torch
+    t0 = time.perf_counter()
+    lat, fin, n = [], [], 0
+    deadline = (stream[-1][0] if stream else 0.0) + drain
+    for a, m in stream:
+        now = time.perf_counter() - t0
+        if now > deadline:
+            break
+        if a > now:
+            time.sleep(a - now)
+        c = g.Context.from_microstructure(m, precision="fp64", tol=1e-10)
+        c.bounds()
+        c.close()
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        if t_measure0 <= a < t_measure1:
+            n += 1
+            lat.append(tf - a)
+            fin.append(tf)
+    wall = time.perf_counter() - t0
+    meas = [a for a, _ in stream if t_measure0 <= a < t_measure1]
+    # requests never started before the cutoff enter with their age at the cutoff
+    lat += [wall - a for a in meas[n:]]
+    window = max(fin) - t_measure0 if fin else float("nan")
+    return {"submitted": len(meas), "completed": n, "unfinished_at_cutoff": len(meas) - n,
+            "latency_ms": _percentiles(lat), "mean_latency_ms": 1e3 * sum(lat) / len(lat) if lat else None,
+            "bound_pairs_per_s": n / window if fin else 0.0, "wall_s": wall}
+
+
+def run_served(args, g):
+    """Poisson arrivals of bound requests mixing d = 2 disk instances (N odd
+    63..1023) and d = 3 sphere instances (N odd 15..129), 50/50.
+
+    1. capacity: a closed-loop probe (all probe requests submitted at once)
+       gives the service rate C of each arm;
+    2. sustained: arrivals at load x C for a warm-up window plus the measured
+       window; latency = arrival -> result (host clock) of the requests that
+       arrived in the measured window, throughput = their completions / time;
+    3. overload (mixed only): the 200 req/s stream for a short window, labelled
+       as such -- one GPU does not sustain it, so its latencies are queueing.
+    Mixed = the batch engine (continuous batching); FP64 = one plain FP64
+    context per request, in arrival order."""
+    import torch
+    out = {"mix": "50% d2 disks N odd 63..1023 (contrast 2..1e4), 50% d3 spheres N odd 15..129 "
+                  "(contrast 2..1e3)", "slots": args.serve_slots}
+    # 1. capacity of the mixed arm (closed loop)
+    probe = [m for _, m in _serve_stream(1e6, args.serve_probe / 1e6, 7)][: args.serve_probe]
+    b = g.Batch(max_active=args.serve_slots)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in probe:
+        b.submit(m)
+    b.run(iterations=4)
+    cap = len(probe) / (time.perf_counter() - t0)
+    b.results()
+    b.close()
+    rate = args.serve_load * cap
+    W0, W1 = args.serve_warmup, args.serve_warmup + args.serve_seconds
+    st = _serve_stream(rate, W1, 11)
+    out["mixed"] = {"capacity_pairs_per_s": cap, "probe_requests": len(probe), "rate_req_per_s": rate,
+                    "measured_window_s": args.serve_seconds, "warmup_s": W0,
+                    **_serve_mixed(g, st, args.serve_slots, W0, W1, args.serve_drain)}
+    if args.serve_overload_rate > 0:
+        so = _serve_stream(args.serve_overload_rate, args.serve_overload_seconds, 13)
+        out["overload"] = {"rate_req_per_s": args.serve_overload_rate,
+                           "window_s": args.serve_overload_seconds,
+                           "note": "beyond one GPU's capacity: latencies are queueing times",
+                           **_serve_mixed(g, so, args.serve_slots, 0.0, args.serve_overload_seconds,
+                                          args.serve_drain)}
+    if args.serve_fp64_seconds > 0:
+        probe64 = probe[: max(4, args.serve_probe // 4)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m in probe64:
+            c = g.Context.from_microstructure(m, precision="fp64", tol=1e-10)
+            c.bounds()
+            c.close()
+        torch.cuda.synchronize()
+        cap64 = len(probe64) / (time.perf_counter() - t0)
+        rate64 = args.serve_load * cap64
+        W1f = args.serve_warmup + args.serve_fp64_seconds
+        s64 = _serve_stream(rate64, W1f, 17)
+        out["fp64"] = {"capacity_pairs_per_s": cap64, "probe_requests": len(probe64), "rate_req_per_s": rate64,
+                       "measured_window_s": args.serve_fp64_seconds, "warmup_s": W0,
+                       **_serve_fp64(g, s64, W0, W1f, args.serve_drain)}
+        out["mixed_vs_fp64_capacity"] = cap / cap64
+    return out
+
+
+def run_d3(args, g, stream):
+    """d = 3 centred sphere (volume fraction 0.2) and centred cube (side 0.6),
+    contrast 1000, at each order of --d3-N: bound pairs/s of the mixed path
+    and of the plain FP64 path, their relative bound difference and
+    grid-pt.iter/s; the axis-2 passes' roofline from the mixed run at the
+    largest order."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    Ns = [int(x) for x in args.d3_N.split(",") if x.strip()]
+    hbm, peak_src = peaks()
+    out = {"workload": "d3 centred sphere vf 0.2 / centred cube side 0.6, contrast 1000, tol 1e-10",
+           "cases": []}
+    for shape in ("sphere", "cube"):
+        for N in Ns:
+            m = W.centred_sphere(N, fraction=0.2, value=1000.0) if shape == "sphere" else \
+                W.centred_cube(N, side=0.6, value=1000.0)
+            cm = g.Context.from_microstructure(m, precision="mixed", tol=1e-10)
+            cm.set_stream(stream)
+            cm.bounds()                            # first launches, plans
+            prof = N == max(Ns) and shape == "sphere"
+            torch.cuda.synchronize()
+            if prof:
+                cm.profile(True)
+            t0 = time.perf_counter()
+            U, L, inf, _ = cm.bounds()
+            torch.cuda.synchronize()
+            tm = time.perf_counter() - t0
+            rec = {"shape": shape, "N": N, "M": cm.M, "mixed_pairs_per_s": 1.0 / tm,
+                   "mixed_grid_pt_iter_per_s": _grid_pt_iters(cm.M, inf, 3) / tm,
+                   "mixed_inner_iters": sum(i["iters"] for i in inf), "upper_00": U[0, 0], "lower_00": L[0, 0]}
+            if prof:
+                pr = cm.profile_read()
+                cm.profile(False)
+                roof = {}
+                for k in ("col2_inv_f32", "col2_fwd_f32", "col1_inv_pupdate_f32", "row_matvec_f32", "col1_fwd_f32"):
+                    v = pr.get(k)
+                    if v and v["launches"]:
+                        avg = v["ms"] / v["launches"] / 1e3
+                        ach = v["bytes"] / avg / 1e9
+                        roof[k] = {"avg_us": 1e6 * avg, "achieved_GBps": ach, "frac": ach / hbm}
+                out["roofline_N%d" % N] = {"peak_GBps": hbm, "peak_source": peak_src, "kernels": roof}
+            cm.close()
+            if N <= args.d3_fp64_max_N:
+                c64 = g.Context.from_microstructure(m, precision="fp64", tol=1e-10)
+                c64.set_stream(stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                U64, L64, inf64, _ = c64.bounds()
+                torch.cuda.synchronize()
+                t64 = time.perf_counter() - t0
+                c64.close()
+                rec.update({"fp64_pairs_per_s": 1.0 / t64,
+                            "fp64_grid_pt_iter_per_s": _grid_pt_iters(c64.M, inf64, 3) / t64,
+                            "mixed_speedup": t64 / tm,
+                            "rel_err_upper": float(np.abs(U - U64).max() / np.abs(U64).max()),
+                            "rel_err_lower": float(np.abs(L - L64).max() / np.abs(L64).max())})
+            out["cases"].append(rec)
+    return out
 
 
 def traffic_for(kernel_name):

@@ -371,7 +371,8 @@ ghb_status ghb_gram_noalloc(int d, const int* N, const int* M, const double* gri
  *   cfg[2] rows32  rows per CTA of the FP32 2-D last-axis pass (0 = size rule,
  *                  1 or 2)
  *   cfg[3] ct_col  1: size-specialised FP32 column kernels (only for lengths
- *                  that have them: 162, 486, 1458, 4374), 0: runtime plan
+ *                  that have them: 72, 135, 162, 270, 486, 1458, 2187,
+ *                  4374), 0: runtime plan
  *   cfg[4] ct_row  the same for the last-axis pass
  *   cfg[5] cap64   as cap32 for FP64
  *   cfg[6] tile64  as tile32 for FP64

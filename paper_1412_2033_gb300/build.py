@@ -20,7 +20,8 @@ BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["col_f32_a.cu", "col_f32_b.cu", "col_f64_a.cu", "col_f64_b.cu", "row_f32.cu", "row_f64.cu",
            "passes.cu", "plan.cu", "fields.cu", "api.cu", "batch.cu", "noalloc.cu",
            "ct_162.cu", "ct_486.cu", "ct_1458.cu", "ct_4374.cu", "ct_2187.cu",
-           "ct64_162.cu", "ct64_486.cu", "ct64_1458.cu", "ct64_4374.cu", "ct64_2187.cu", "tune.cu"]
+           "ct64_162.cu", "ct64_486.cu", "ct64_1458.cu", "ct64_4374.cu", "ct64_2187.cu",
+           "ct_72.cu", "ct_135.cu", "ct_270.cu", "ct64_72.cu", "ct64_135.cu", "ct64_270.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

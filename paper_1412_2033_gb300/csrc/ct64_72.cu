@@ -1,0 +1,10 @@
+// Size-specialised FP64 operator passes for the transform length M = 72
+// (a double grid of the 3-D operator; see fft_ct.cuh and passes_impl.cuh).
+#include "passes_impl.cuh"
+
+namespace ghb {
+
+template ghb_status launch_col_ct_m<double, 72>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
+template ghb_status launch_row_ct_m<double, 72>(int, const RowArgs&, const FftPlan&, int, cudaStream_t);
+
+}  // namespace ghb

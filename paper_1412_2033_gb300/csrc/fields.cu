@@ -618,24 +618,79 @@ template ghb_status launch_rhs<double>(void*, const double2*, const Geometry&, c
 // where (A v_i)^(k) = a^(k) E_i + y_i(k) and y_i is the operator output of x_i
 // before the projection (pad, inverse transform, A_M, forward transform,
 // truncation to Z_N).  v_j vanishes outside Z_N, so this is the exact energy
-// the double-grid evaluation gives.  Per-block partial sums of the d^2 entries
-// in FP64, then one block adds the partials in block order.
+// the double-grid evaluation gives.
+//
+// At high contrast the terms of this sum cancel (the field is small where the
+// coefficient is large), so the sum is carried as an unevaluated pair
+// hi + lo of doubles (Knuth's TwoSum, error-free): every product is rounded
+// once and the sum of the rounded products is exact up to one final rounding,
+// per thread, across a warp, across a block and across blocks (in block
+// order).
 // ---------------------------------------------------------------------------
+struct DD {
+  double hi, lo;
+};
+// hi + lo = a + b exactly (TwoSum)
+__device__ __forceinline__ DD two_sum(double a, double b) {
+  const double s = a + b;
+  const double bb = s - a;
+  const double err = (a - (s - bb)) + (b - bb);
+  return DD{s, err};
+}
+__device__ __forceinline__ void dd_add(DD& acc, double x) {
+  const DD t = two_sum(acc.hi, x);
+  acc.hi = t.hi;
+  acc.lo += t.lo;
+}
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  DD t = two_sum(a.hi, b.hi);
+  t.lo += a.lo + b.lo;
+  return two_sum(t.hi, t.lo);
+}
+__device__ __forceinline__ DD dd_warp_sum(DD v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DD w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = dd_add(v, w);
+  }
+  return v;
+}
+// Block sum of one pair per thread (valid in thread 0); barriers inside.
+__device__ __forceinline__ DD dd_block_sum(DD v, double* sh /* 64 doubles */) {
+  v = dd_warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sh[wid] = v.hi;
+    sh[32 + wid] = v.lo;
+  }
+  __syncthreads();
+  DD r{0.0, 0.0};
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane < nw) r = DD{sh[lane], sh[32 + lane]};
+    r = dd_warp_sum(r);
+  }
+  return r;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kFieldThreads) gram_zn_kernel(GramZnArgs ga, const double2* __restrict__ tab,
                                                                 Geometry g, FieldGeom fg, double* partials) {
-  __shared__ double red[32];
+  __shared__ double red[64];
   const int Ld = g.N[D - 1];
   const int L1 = 2 * g.N[1] - 1;
-  double acc[D * D];
+  DD acc[D * D];
 #pragma unroll
-  for (int q = 0; q < D * D; ++q) acc[q] = 0.0;
+  for (int q = 0; q < D * D; ++q) acc[q] = DD{0.0, 0.0};
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < fg.P;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     int k[3];
     int j;
     kvec(fg, e, k, j);
-    const double wt = (j == 0) ? 1.0 : 2.0;
+    const double wt = (j == 0) ? 1.0 : 2.0;   // exact scaling: the mirrored half
     int64_t ti;
     if (D == 2) ti = static_cast<int64_t>(k[0] + g.N[0] - 1) * Ld + j;
     else ti = (static_cast<int64_t>(k[0] + g.N[0] - 1) * L1 + (k[1] + g.N[1] - 1)) * Ld + j;
@@ -655,29 +710,35 @@ __global__ void __launch_bounds__(kFieldThreads) gram_zn_kernel(GramZnArgs ga, c
 #pragma unroll
       for (int c = 0; c < D; ++c) av[c] = (c == i) ? make_double2(y[i][c].x + a.x, y[i][c].y + a.y) : y[i][c];
 #pragma unroll
-      for (int jf = 0; jf < D; ++jf) {
-        double sre = 0.0;
+      for (int jf = 0; jf < D; ++jf)
 #pragma unroll
-        for (int c = 0; c < D; ++c) sre += av[c].x * v[jf][c].x + av[c].y * v[jf][c].y;
-        acc[i * D + jf] += wt * sre;
-      }
+        for (int c = 0; c < D; ++c) {
+          dd_add(acc[i * D + jf], wt * (av[c].x * v[jf][c].x));
+          dd_add(acc[i * D + jf], wt * (av[c].y * v[jf][c].y));
+        }
     }
   }
+  const int64_t nb = gridDim.x;
 #pragma unroll
   for (int q = 0; q < D * D; ++q) {
-    const double bs = block_sum(acc[q], red);
-    if (threadIdx.x == 0) partials[static_cast<int64_t>(q) * gridDim.x + blockIdx.x] = bs;
+    const DD bs = dd_block_sum(acc[q], red);
+    if (threadIdx.x == 0) {
+      partials[(2 * static_cast<int64_t>(q)) * nb + blockIdx.x] = bs.hi;
+      partials[(2 * static_cast<int64_t>(q) + 1) * nb + blockIdx.x] = bs.lo;
+    }
   }
 }
 
 __global__ void __launch_bounds__(kFieldThreads) gram_zn_final(const double* __restrict__ partials, int nb, int dd,
                                                                double* out) {
-  __shared__ double red[32];
+  __shared__ double red[64];
   for (int q = 0; q < dd; ++q) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[static_cast<int64_t>(q) * nb + b];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) out[q] = s;
+    DD s{0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      s = dd_add(s, DD{partials[(2 * static_cast<int64_t>(q)) * nb + b],
+                       partials[(2 * static_cast<int64_t>(q) + 1) * nb + b]});
+    s = dd_block_sum(s, red);
+    if (threadIdx.x == 0) out[q] = s.hi + s.lo;
   }
 }
 
@@ -686,7 +747,7 @@ ghb_status launch_gram_zn(const GramZnArgs& ga, const double2* tab, const Geomet
   const FieldGeom fg = make_field_geom(g.d, g.N[0], g.N[1], g.N[2], g.h, g.P);
   const int dd = g.d * g.d;
   int nb = field_grid(g.P);
-  if (nb * dd > max_partials) nb = max_partials / dd;
+  if (2 * nb * dd > max_partials) nb = max_partials / (2 * dd);   // hi and lo per block and entry
   if (g.d == 2) gram_zn_kernel<2><<<nb, kFieldThreads, 0, s>>>(ga, tab, g, fg, partials);
   else gram_zn_kernel<3><<<nb, kFieldThreads, 0, s>>>(ga, tab, g, fg, partials);
   GHB_CUDA_TRY(cudaGetLastError());

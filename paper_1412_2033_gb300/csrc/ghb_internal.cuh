@@ -26,6 +26,13 @@ void set_error(const std::string& msg);
     }                                                                          \
   } while (0)
 
+// Return a failing ghb_status from the enclosing function.
+#define TRY_STATUS(expr)                 \
+  do {                                   \
+    const ghb_status st__ = (expr);      \
+    if (st__ != GHB_OK) return st__;     \
+  } while (0)
+
 // ---------------------------------------------------------------------------
 // device-side CG scalars (one per running solve)
 // ---------------------------------------------------------------------------
@@ -326,9 +333,10 @@ __host__ __device__ constexpr int col_tile_width(int M, int elem_bytes) {
 
 // Transform lengths with size-specialised FP32 and FP64 operator kernels
 // (fft_ct.cuh): the double grids 2 * 3^k of the 2-D operator at N = 81, 243,
-// 729, 2187, and 2187 itself (the reduced operator's transforms at N = 2187).
+// 729, 2187, 2187 itself (the reduced operator's transforms at N = 2187), and
+// the double grids 72, 135, 270 of the 3-D operator at N = 33, 65, 129.
 __host__ __device__ constexpr bool ct_size(int M) {
-  return M == 162 || M == 486 || M == 1458 || M == 4374 || M == 2187;
+  return M == 162 || M == 486 || M == 1458 || M == 4374 || M == 2187 || M == 72 || M == 135 || M == 270;
 }
 template <typename T>
 ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);

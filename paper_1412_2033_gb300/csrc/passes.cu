@@ -14,6 +14,7 @@
 //                             (1/|M|) sum_m A_M(x_m) v_i(x_m).v_j(x_m).
 //                   Two real lines share one complex transform (z = u + i v).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "ghb_internal.cuh"
@@ -44,6 +45,9 @@ ghb_status launch_col_ct(int sign, int mode, const ColArgs& a, const FftPlan& pl
     case 1458: return launch_col_ct_m<T, 1458>(sign, mode, a, pl, s);
     case 4374: return launch_col_ct_m<T, 4374>(sign, mode, a, pl, s);
     case 2187: return launch_col_ct_m<T, 2187>(sign, mode, a, pl, s);
+    case 72: return launch_col_ct_m<T, 72>(sign, mode, a, pl, s);
+    case 135: return launch_col_ct_m<T, 135>(sign, mode, a, pl, s);
+    case 270: return launch_col_ct_m<T, 270>(sign, mode, a, pl, s);
     default: break;
   }
   set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
@@ -60,6 +64,9 @@ ghb_status launch_row_ct(int NL, const RowArgs& a, const FftPlan& pl, int rows_p
     case 1458: return launch_row_ct_m<T, 1458>(NL, a, pl, rows_per_cta, s);
     case 4374: return launch_row_ct_m<T, 4374>(NL, a, pl, rows_per_cta, s);
     case 2187: return launch_row_ct_m<T, 2187>(NL, a, pl, rows_per_cta, s);
+    case 72: return launch_row_ct_m<T, 72>(NL, a, pl, rows_per_cta, s);
+    case 135: return launch_row_ct_m<T, 135>(NL, a, pl, rows_per_cta, s);
+    case 270: return launch_row_ct_m<T, 270>(NL, a, pl, rows_per_cta, s);
     default: break;
   }
   set_error("internal: no size-specialised kernels for M=" + std::to_string(pl.M));
@@ -84,12 +91,14 @@ bool use_ct(const FftPlan& pl, bool tuned_on) {
 // with the most CTAs.  Wide operands (the axis-1 pass in 3-D) get wide tiles,
 // narrow ones (2-D operands of small N) narrow ones.
 int auto_tile(int M, int64_t outer, int64_t inner, int elem_bytes) {
-  static int sms = 0;
+  static std::atomic<int> sms_cache{0};   // SM count (one device model per process)
+  int sms = sms_cache.load(std::memory_order_relaxed);
   if (sms == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
       sms = 152;
+    sms_cache.store(sms, std::memory_order_relaxed);
   }
   int fallback = 0;
   for (int tw : {16, 8, 4, 2, 1}) {

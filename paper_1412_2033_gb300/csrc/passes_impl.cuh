@@ -18,7 +18,9 @@
 // precision and tile-width group) so that the library compiles in parallel.
 #pragma once
 
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "fft_ct.cuh"
 #include "ghb_internal.cuh"
@@ -43,6 +45,22 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // wait until at most N of this thread's committed groups are still in flight
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The dynamic shared-memory limit of kernel `func` raised to `bytes` on the
+// current device.  The attribute belongs to the device's context, so it is set
+// once per device (bit `dev` of `mask`, one mask per kernel); two host threads
+// may both set it, which is harmless.  Devices beyond 63 set it every time.
+template <typename F>
+inline ghb_status ensure_dyn_smem(F* func, int bytes, std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  GHB_CUDA_TRY(cudaGetDevice(&dev));
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit == 0 || !(mask.load(std::memory_order_acquire) & bit)) {
+    GHB_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    mask.fetch_or(bit, std::memory_order_release);
+  }
+  return GHB_OK;
+}
 
 // Shared-memory index of entry i: padded for the runtime-plan transform,
 // plain for the size-specialised one (MCT = its compile-time length).
@@ -306,12 +324,8 @@ template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
 inline ghb_status launch_col_t(const ColArgs& a, const FftPlan& pl, cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t smem = col_smem_bytes(pl.M, TW, sizeof(C));
-  static bool attr_set = false;
-  if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(col_kernel<T, TW, SIGN, MODE, MCT>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_mask{0};
+  TRY_STATUS(ensure_dyn_smem(col_kernel<T, TW, SIGN, MODE, MCT>, 220 * 1024, attr_mask));
   const int64_t tiles = (a.inner + TW - 1) / TW;
   const int64_t grid = tiles * a.outer;
   const int threads = MCT != 0 ? col_threads<T, TW, MCT>()
@@ -333,12 +347,8 @@ ghb_status launch_col_tw(int sign, int mode, const ColArgs& a, const FftPlan& pl
 template <typename T, int TW, int SIGN, int MODE>
 inline ghb_status launch_col_batch_t(const ColItem* items, int n, int64_t blocks, size_t smem,
                                      cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(col_kernel_batch<T, TW, SIGN, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_mask{0};
+  TRY_STATUS(ensure_dyn_smem(col_kernel_batch<T, TW, SIGN, MODE>, 220 * 1024, attr_mask));
   const int threads = sizeof(T) == 4 ? kColThreads32 : kColThreads64;
   col_kernel_batch<T, TW, SIGN, MODE><<<static_cast<unsigned>(blocks), threads, smem, s>>>(items, n);
   GHB_CUDA_TRY(cudaGetLastError());
@@ -734,12 +744,8 @@ __global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? 3 : 1)
 template <typename T, int NL, int MODE>
 inline ghb_status launch_row_batch_t(const RowItem* items, int n, int64_t blocks, size_t smem,
                                      cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(row_kernel_batch<T, NL, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_mask{0};
+  TRY_STATUS(ensure_dyn_smem(row_kernel_batch<T, NL, MODE>, 200 * 1024, attr_mask));
   row_kernel_batch<T, NL, MODE><<<static_cast<unsigned>(blocks), kRowThreads, smem, s>>>(items, n);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
@@ -750,12 +756,8 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
                                cudaStream_t s) {
   using C = typename CT<T>::type;
   const size_t smem = padded_elems<C>(static_cast<size_t>(pl.M) * NL) * sizeof(C);
-  static bool attr_set = false;
-  if (!attr_set) {
-    GHB_CUDA_TRY(cudaFuncSetAttribute(row_kernel<T, NL, MODE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_mask{0};
+  TRY_STATUS(ensure_dyn_smem(row_kernel<T, NL, MODE>, 200 * 1024, attr_mask));
   if (smem > 200 * 1024) {
     set_error("row transform too large for one CTA: M=" + std::to_string(pl.M));
     return GHB_ERR_INVALID;
@@ -765,19 +767,32 @@ inline ghb_status launch_row_t(const RowArgs& a, const FftPlan& pl, int rows_per
     const size_t ssmem =
         row_staged_smem<T, NL>(pl.M, a.H, row_streams_multiplier<T, MCT>() ? 0 : rows_per_cta);
     if (ssmem <= 200 * 1024) {
-      // persistent grid: as many CTAs as fit on the device at once
-      static int per_sm = 0, sms = 0;
-      static size_t per_sm_smem = 0;
-      if (per_sm_smem != ssmem) {
-        GHB_CUDA_TRY(cudaFuncSetAttribute(row_kernel_staged<T, NL, MCT>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        GHB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_kernel_staged<T, NL, MCT>,
-                                                                   row_threads<T, MCT>(), ssmem));
-        int dev = 0;
-        GHB_CUDA_TRY(cudaGetDevice(&dev));
-        GHB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        per_sm_smem = ssmem;
+      // persistent grid: as many CTAs as fit on the device at once (the
+      // occupancy per device and staging size, kept per device)
+      static std::atomic<unsigned long long> staged_mask{0};
+      TRY_STATUS(ensure_dyn_smem(row_kernel_staged<T, NL, MCT>, 200 * 1024, staged_mask));
+      struct Occ {
+        size_t smem;
+        int per_sm, sms;
+      };
+      static std::mutex occ_mutex;
+      static Occ occ[64] = {};
+      int dev = 0;
+      GHB_CUDA_TRY(cudaGetDevice(&dev));
+      Occ o{0, 0, 0};
+      {
+        std::lock_guard<std::mutex> lock(occ_mutex);
+        if (dev < 64) o = occ[dev];
       }
+      if (o.smem != ssmem) {
+        o.smem = ssmem;
+        GHB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, row_kernel_staged<T, NL, MCT>,
+                                                                   row_threads<T, MCT>(), ssmem));
+        GHB_CUDA_TRY(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev));
+        std::lock_guard<std::mutex> lock(occ_mutex);
+        if (dev < 64) occ[dev] = o;
+      }
+      const int per_sm = o.per_sm, sms = o.sms;
       int64_t grid = static_cast<int64_t>(per_sm > 0 ? per_sm : 1) * sms;
       if (grid > groups) grid = groups;
       if (grid < 1) grid = 1;

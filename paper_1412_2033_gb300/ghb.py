@@ -400,14 +400,33 @@ class Context:
 def gram_noalloc(d, N, M, grid, fields, stream=None):
     """ghb_gram_noalloc: the Gram matrix of FP64 half-spectrum fields without any
     device allocation (scratch in a fixed 32 MiB device array; for callers that
-    cannot allocate).  grid: FP64 CUDA tensor of the double-grid values."""
+    cannot allocate).  grid: FP64 CUDA tensor of the double-grid values (prod(M)
+    entries); fields: 1..d complex128 CUDA tensors of d * N_1 ... N_{d-1} *
+    (N_d + 1)/2 entries each, contiguous, on the current device."""
+    import torch
     lib = load_library()
+    d = int(d)
+    if d not in (2, 3) or len(N) != d or len(M) != d:
+        raise ValueError("d must be 2 or 3 with d orders N and d double-grid sizes M")
+    if not 1 <= len(fields) <= d:
+        raise ValueError(f"between 1 and d = {d} fields are allowed, got {len(fields)}")
+    dev = torch.cuda.current_device()
+
+    def check(t, dtype, n, what):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.dtype == dtype
+                and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"{what} must be a contiguous {dtype} tensor of {n} entries on cuda:{dev}")
+
+    check(grid, torch.float64, int(np.prod([int(m) for m in M])), "grid")
+    nf = d * int(np.prod([int(n) for n in N[:-1]])) * ((int(N[-1]) + 1) // 2)
+    for f in fields:
+        check(f, torch.complex128, nf, "each field")
     Nc = (ctypes.c_int * 3)(*([int(n) for n in N] + [1] * (3 - len(N))))
     Mc = (ctypes.c_int * 3)(*([int(n) for n in M] + [1] * (3 - len(M))))
     ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in fields])
     out = (ctypes.c_double * 9)()
     s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-    _check(lib.ghb_gram_noalloc(int(d), Nc, Mc, ctypes.c_void_p(grid.data_ptr()), len(fields), ptrs, out, s))
+    _check(lib.ghb_gram_noalloc(d, Nc, Mc, ctypes.c_void_p(grid.data_ptr()), len(fields), ptrs, out, s))
     m = len(fields)
     return np.array(out[: m * m]).reshape(m, m)
 

@@ -6,14 +6,16 @@ N = 729 values, square symmetry, Voigt/Reuss and Hashin-Shtrikman brackets).
 
 Tolerances: FP64 path 1e-12 relative (the FP64 parity target); mixed path
 1e-8 relative with the upper bound not below and the lower bound not above
-the oracle by more than max(1e-13, 1e-15 x contrast) relative (FP64
-evaluation noise of the energies grows with the contrast).
+the oracle by more than the one-sided slack of tests/conftest.py (1e-13)
+relative.
 """
 import json
 import os
 
 import numpy as np
 import pytest
+
+from conftest import one_sided_margins, one_sided_slack
 
 import workloads as W
 from oracle import coefficients as OC
@@ -37,16 +39,6 @@ def ghb():
     return g
 
 
-def one_sided_slack(m):
-    """Relative slack of the one-sided checks.  The exact energy of an
-    admissible field can never undercut the minimum, but its FP64 evaluation on
-    the double grid carries rounding of about eps log2|M| rho_A relative, rho_A
-    the contrast (the oracle's own bounds move by 1.7e-13 between two
-    admissible M at rho_A = 4e3): max(1e-13, 1e-15 rho_A)."""
-    vals = [m["a0"]] + [inc[3] for inc in m["inclusions"]]
-    return max(1e-13, 1e-15 * max(vals) / min(vals))
-
-
 def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
 
@@ -64,9 +56,9 @@ def test_golden_bounds(ghb, name, prec):
         assert rel(U, Uo) < 1e-12 and rel(L, Lo) < 1e-12
     else:
         assert rel(U, Uo) < 1e-8 and rel(L, Lo) < 1e-8
-        sl = one_sided_slack(m)
-        for i in range(m["d"]):
-            assert U[i, i] >= Uo[i, i] * (1 - sl) and L[i, i] <= Lo[i, i] * (1 + sl)
+        su, sl = one_sided_slack(m)
+        mu, ml = one_sided_margins(U, L, Uo, Lo)
+        assert mu >= -su and ml >= -sl, (mu, ml, su, sl)
 
 
 def _hs(a1, a2, f2, d):

@@ -8,12 +8,14 @@ Tolerances:
   about 20 radix stages and the conditioning of the multiply).
 * FP64 bounds: 1e-12 relative (the stated FP64 parity target).
 * Mixed bounds: 1e-8 relative, upper >= oracle (1 - s), lower <= oracle (1 + s)
-  with s = max(1e-13, 1e-15 x contrast) (FP64 evaluation noise of the energies).
+  with s the one-sided slack of tests/conftest.py (1e-13).
 """
 import zlib
 
 import numpy as np
 import pytest
+
+from conftest import one_sided_margins, one_sided_slack
 
 import workloads as W
 from oracle import coefficients as OC
@@ -28,16 +30,6 @@ def ghb():
     import paper_1412_2033_gb300 as g
     g.load_library()
     return g
-
-
-def one_sided_slack(m):
-    """Relative slack of the one-sided checks.  The exact energy of an
-    admissible field can never undercut the minimum, but its FP64 evaluation on
-    the double grid carries rounding of about eps log2|M| rho_A relative, rho_A
-    the contrast (the oracle's own bounds move by 1.7e-13 between two
-    admissible M at rho_A = 4e3): max(1e-13, 1e-15 rho_A)."""
-    vals = [m["a0"]] + [inc[3] for inc in m["inclusions"]]
-    return max(1e-13, 1e-15 * max(vals) / min(vals))
 
 
 def rel(a, b):
@@ -184,11 +176,10 @@ def test_bounds_mixed_parity_and_one_sided(ghb, name):
     Uo, Lo, _ = OG.bounds(oracle_material(spec), spec["N"], M=ctx.M, tol=1e-12)
     assert rel(U, Uo) < 1e-8 and rel(L, Lo) < 1e-8
     d = spec["d"]
-    sl = one_sided_slack(spec)
-    for i in range(d):
-        assert U[i, i] >= Uo[i, i] * (1 - sl)
-        assert L[i, i] <= Lo[i, i] * (1 + sl)
-    assert np.all(np.linalg.eigvalsh(U - Uo) > -sl * np.abs(Uo).max())
+    su, sl = one_sided_slack(spec)
+    mu, ml = one_sided_margins(U, L, Uo, Lo)
+    assert mu >= -su and ml >= -sl, (mu, ml, su, sl)
+    assert np.all(np.linalg.eigvalsh(U - Uo) > -su * np.abs(Uo).max())
     assert any(i["matvecs_fp32"] > 0 for i in infos)
 
 
@@ -292,24 +283,30 @@ def test_matvec_full_size_sampled(ghb, N, prec):
     assert np.abs(got - ref).max() < (1e-11 if prec == "f64" else 2e-5) * scale
 
 
+# (N, double grid): the 3-D orders of the sphere/cube family and their
+# size-specialised transform lengths 72 = 3^2 4 2, 135 = 5 3^3, 162 = 3^4 2,
+# 270 = 5 3^3 2
+D3_SIZES = [(33, 72), (65, 135), (81, 162), (129, 270)]
+
+
+@pytest.mark.parametrize("N,M", D3_SIZES)
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_matvec_3d_specialised_sampled(ghb, prec):
-    """d = 3 at N = 81 (M = 162 on every axis): the size-specialised column
-    passes on both non-contiguous axes and the last-axis pass with three
-    interleaved lines per CTA (FP32: A_M read in the fused pass), at sampled
-    output frequencies against the oracle's definition
+def test_matvec_3d_specialised_sampled(ghb, N, M, prec):
+    """d = 3 at N = 33 ... 129 (M = 72 ... 270 on every axis): the
+    size-specialised column passes on both non-contiguous axes and the
+    last-axis pass with three interleaved lines per CTA (FP32: A_M read in the
+    fused pass), at sampled output frequencies against the oracle's definition
     y(l) = G(l) sum_k a^(l - k) x(k), primal and dual."""
-    N = 81
     m = W.centred_sphere(N, fraction=0.2, value=1000.0)
     m["inclusions"].append((0, (0.38, -0.35, 0.33), (0.15, 0.2, 0.12), 0.3))   # a box clear of the sphere
     mat = OC.material_from_dict(m)
     ctx = ghb.Context.from_microstructure(m)
-    assert ctx.M == [2 * N] * 3
+    assert ctx.M == [M] * 3
     x = W.random_field(np.random.default_rng(3 * N), 3, [N, N, N])
     dt = torch.complex128 if prec == "f64" else torch.complex64
     xt = torch.from_numpy(np.ascontiguousarray(ghb.half_from_full(x))).to(dt).cuda()
     c = (N - 1) // 2
-    idx = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 1], [-c, c, c], [c, -3, 0], [7, -c, 11], [-19, 23, c]])
+    idx = np.array([[0, 0, 0], [1, 0, 0], [0, 0, 1], [-c, c, c], [c, -3, 0], [7, -c, 11], [-13, 12, c]])
     for kind, okind in ((ghb.GHB_PRIMAL, OG.PRIMAL), (ghb.GHB_DUAL, OG.DUAL)):
         y = ctx.matvec(xt, kind=kind).cpu().numpy()
         ref = OG.matvec_sampled(x, mat if okind == OG.PRIMAL else mat.inverse(), okind, idx)
@@ -317,3 +314,26 @@ def test_matvec_3d_specialised_sampled(ghb, prec):
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() < (1e-11 if prec == "f64" else 2e-5) * scale, (prec, kind)
 
+
+# ragged 3-D orders that put one size-specialised length (M = 270 or 135) on
+# each axis in turn, the others on runtime plans: every entry against the
+# oracle's double-grid operator
+RAGGED_3D = [([129, 9, 7], [270, 18, 15]), ([7, 129, 9], [15, 270, 18]), ([9, 7, 129], [18, 15, 270]),
+             ([65, 11, 9], [135, 24, 18])]
+
+
+@pytest.mark.parametrize("N,M", RAGGED_3D)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matvec_3d_ragged_specialised(ghb, N, M, prec):
+    m = dict(d=3, N=N, a0=1.0, inclusions=[(2, (0.1, -0.05, 0.2), (0.27, 0, 0), 40.0),
+                                            (0, (-0.3, 0.3, -0.3), (0.2, 0.15, 0.1), 0.5)])
+    ctx = ghb.Context.from_microstructure(m)
+    assert ctx.M == M
+    mat = OC.material_from_dict(m)
+    x = W.random_field(np.random.default_rng(sum(N)), 3, N)
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    xt = torch.from_numpy(np.ascontiguousarray(ghb.half_from_full(x))).to(dt).cuda()
+    for kind, okind in ((ghb.GHB_PRIMAL, OG.PRIMAL), (ghb.GHB_DUAL, OG.DUAL)):
+        ref = ghb.half_from_full(OG.Operator(mat, N, okind, M=M).apply(x))
+        got = ctx.matvec(xt, kind=kind).cpu().numpy()
+        assert rel(got, ref) < (1e-12 if prec == "f64" else 2e-5), (prec, kind)
