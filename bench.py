@@ -83,6 +83,9 @@ def parse():
                     help="requests the server solves at once (more wait in its queue)")
     ap.add_argument("--serve-fp64-seconds", type=float, default=20.0,
                     help="measured arrival window of the plain FP64 served run (0 = skip)")
+    ap.add_argument("--matvec-workload", choices=["disk", "sphere"], default="disk",
+                    help="--matvec-only: the d = 2 disk (default) or the d = 3 sphere of volume fraction 0.2, "
+                         "contrast 1000, at order --N")
     ap.add_argument("--matvec-only", choices=["f32", "f64"], default=None,
                     help="only apply the operator (warmup + steps times) at the workload size; "
                          "prints the mean time per application (used for ncu captures)")
@@ -886,7 +889,7 @@ def run_matvec_only(args, local):
     import workloads as W
 
     torch.cuda.set_device(local)
-    m = workload(args.N)
+    m = workload(args.N) if args.matvec_workload == "disk" else W.centred_sphere(args.N, fraction=0.2, value=1000.0)
     ctx = g.Context.from_microstructure(m)
     dt = torch.complex64 if args.matvec_only == "f32" else torch.complex128
     x = torch.from_numpy(np.ascontiguousarray(g.half_from_full(

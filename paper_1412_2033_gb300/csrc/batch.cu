@@ -155,6 +155,7 @@ struct Launch {
   int kind;             // 0 col, 1 row, 2 cg
   bool f32;
   int sign, mode, op, tile;   // tile: TW (col) or NL (row)
+  int threads;                // threads per CTA (0 = the kernel's full block)
   const void* items;
   int n;
   int64_t blocks;
@@ -396,6 +397,21 @@ ghb_status prep_cg(ghb_batch* b, int op, std::vector<CgItem>& items, std::vector
   return GHB_OK;
 }
 
+// Threads per CTA of a batched transform pass over `lines` interleaved lines
+// of length at most Mmax: about one thread per butterfly of a pass (a pass
+// combines up to 32 entries in FP32 and 18 in FP64, so a line has at least
+// Mmax / 32 or Mmax / 18 of them), in whole warps, at least 64.  Short
+// transforms then run several CTAs per SM instead of one CTA whose threads
+// mostly wait.
+template <typename T>
+int batch_threads(int Mmax, int lines, int full) {
+  const int cap = sizeof(T) == 4 ? 32 : 18;
+  const int units = (Mmax + cap - 1) / cap;
+  int t = ((units * lines + 31) / 32) * 32;
+  if (t < 64) t = 64;
+  return t < full ? t : full;
+}
+
 template <typename T>
 ghb_status prep_col(ghb_batch* b, int sign, int mode, std::vector<ColItem>& items, const std::vector<int>& Ms,
                     std::vector<Launch>& out) {
@@ -419,6 +435,7 @@ ghb_status prep_col(ghb_batch* b, int sign, int mode, std::vector<ColItem>& item
   L.sign = sign;
   L.mode = mode;
   L.tile = TW;
+  L.threads = batch_threads<T>(Mmax, TW, sizeof(T) == 4 ? 512 : 256);
   L.n = static_cast<int>(items.size());
   L.blocks = blocks;
   L.smem = col_smem_bytes(Mmax, TW, sizeof(C));
@@ -451,6 +468,7 @@ ghb_status prep_row(ghb_batch* b, int mode, std::vector<RowItem>& items, const s
   L.f32 = sizeof(T) == 4;
   L.mode = mode;
   L.tile = NL;
+  L.threads = mode == ROW_MATVEC ? batch_threads<T>(Mmax, NL, 256) : 0;
   L.n = static_cast<int>(items.size());
   L.blocks = blocks;
   L.smem = padded_elems<C>(static_cast<size_t>(Mmax) * NL) * sizeof(C);
@@ -465,13 +483,13 @@ ghb_status run_launch(ghb_batch* b, const Launch& L) {
   ++b->launches;
   if (L.kind == 0) {
     const ColItem* it = static_cast<const ColItem*>(L.items);
-    return L.f32 ? launch_col_batch<float>(L.sign, L.mode, L.tile, it, L.n, L.blocks, L.smem, b->stream)
-                 : launch_col_batch<double>(L.sign, L.mode, L.tile, it, L.n, L.blocks, L.smem, b->stream);
+    return L.f32 ? launch_col_batch<float>(L.sign, L.mode, L.tile, it, L.n, L.blocks, L.smem, L.threads, b->stream)
+                 : launch_col_batch<double>(L.sign, L.mode, L.tile, it, L.n, L.blocks, L.smem, L.threads, b->stream);
   }
   if (L.kind == 1) {
     const RowItem* it = static_cast<const RowItem*>(L.items);
-    return L.f32 ? launch_row_batch<float>(L.mode, L.tile, it, L.n, L.blocks, L.smem, b->stream)
-                 : launch_row_batch<double>(L.mode, L.tile, it, L.n, L.blocks, L.smem, b->stream);
+    return L.f32 ? launch_row_batch<float>(L.mode, L.tile, it, L.n, L.blocks, L.smem, L.threads, b->stream)
+                 : launch_row_batch<double>(L.mode, L.tile, it, L.n, L.blocks, L.smem, L.threads, b->stream);
   }
   const CgItem* it = static_cast<const CgItem*>(L.items);
   return L.f32 ? launch_cg_batch<float>(L.op, it, L.n, L.blocks, b->stream)

@@ -6,7 +6,7 @@ namespace ghb {
 template ghb_status launch_col_tw<float, 8>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 template ghb_status launch_col_tw<float, 16>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 
-template ghb_status launch_col_batch_tw<float, 8>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
-template ghb_status launch_col_batch_tw<float, 16>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_col_batch_tw<float, 8>(int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
+template ghb_status launch_col_batch_tw<float, 16>(int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
 
 }  // namespace ghb

@@ -7,8 +7,8 @@ template ghb_status launch_col_tw<double, 1>(int, int, const ColArgs&, const Fft
 template ghb_status launch_col_tw<double, 2>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 template ghb_status launch_col_tw<double, 4>(int, int, const ColArgs&, const FftPlan&, cudaStream_t);
 
-template ghb_status launch_col_batch_tw<double, 1>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
-template ghb_status launch_col_batch_tw<double, 2>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
-template ghb_status launch_col_batch_tw<double, 4>(int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_col_batch_tw<double, 1>(int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
+template ghb_status launch_col_batch_tw<double, 2>(int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
+template ghb_status launch_col_batch_tw<double, 4>(int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
 
 }  // namespace ghb

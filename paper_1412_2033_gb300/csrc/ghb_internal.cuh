@@ -189,9 +189,9 @@ struct RowItem {
 // for the largest M of the batch (col_tile_width, row_lines).
 template <typename T>
 ghb_status launch_col_batch(int sign, int mode, int TW, const ColItem* items, int n, int64_t blocks,
-                            size_t smem, cudaStream_t s);
+                            size_t smem, int threads, cudaStream_t s);
 template <typename T>
-ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem,
+ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem, int threads,
                             cudaStream_t s);
 // rows per CTA and interleaved complex lines of a row pass
 // Rows per CTA and interleaved complex lines of a last-axis pass; rows32 is the

@@ -27,10 +27,10 @@ ghb_status launch_col_tw(int sign, int mode, const ColArgs& a, const FftPlan& pl
 template <typename T, int NL, int MODE>
 ghb_status launch_row_nl(const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s);
 template <typename T, int TW>
-ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, int64_t blocks, size_t smem,
+ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, int64_t blocks, size_t smem, int threads,
                                cudaStream_t s);
 template <typename T, int NL, int MODE>
-ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size_t smem, cudaStream_t s);
+ghb_status launch_row_batch_nl(const RowItem* items, int n, int64_t blocks, size_t smem, int threads, cudaStream_t s);
 
 template <typename T, int M>
 ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& pl, cudaStream_t s);
@@ -151,37 +151,37 @@ void row_lines(int mode, int nfields, int ncomp, int M, int rows32, int* rows_pe
 
 template <typename T>
 ghb_status launch_col_batch(int sign, int mode, int TW, const ColItem* items, int n, int64_t blocks,
-                            size_t smem, cudaStream_t s) {
+                            size_t smem, int threads, cudaStream_t s) {
   switch (TW) {
-    case 1: return launch_col_batch_tw<T, 1>(sign, mode, items, n, blocks, smem, s);
-    case 2: return launch_col_batch_tw<T, 2>(sign, mode, items, n, blocks, smem, s);
-    case 4: return launch_col_batch_tw<T, 4>(sign, mode, items, n, blocks, smem, s);
-    case 8: return launch_col_batch_tw<T, 8>(sign, mode, items, n, blocks, smem, s);
-    case 16: return launch_col_batch_tw<T, 16>(sign, mode, items, n, blocks, smem, s);
+    case 1: return launch_col_batch_tw<T, 1>(sign, mode, items, n, blocks, smem, threads, s);
+    case 2: return launch_col_batch_tw<T, 2>(sign, mode, items, n, blocks, smem, threads, s);
+    case 4: return launch_col_batch_tw<T, 4>(sign, mode, items, n, blocks, smem, threads, s);
+    case 8: return launch_col_batch_tw<T, 8>(sign, mode, items, n, blocks, smem, threads, s);
+    case 16: return launch_col_batch_tw<T, 16>(sign, mode, items, n, blocks, smem, threads, s);
     default: break;
   }
   set_error("internal: bad tile width");
   return GHB_ERR_INVALID;
 }
-template ghb_status launch_col_batch<double>(int, int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
-template ghb_status launch_col_batch<float>(int, int, int, const ColItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_col_batch<double>(int, int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
+template ghb_status launch_col_batch<float>(int, int, int, const ColItem*, int, int64_t, size_t, int, cudaStream_t);
 
 template <typename T>
-ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem,
+ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64_t blocks, size_t smem, int threads,
                             cudaStream_t s) {
   if (mode == ROW_MATVEC) {
-    if (NL == 1) return launch_row_batch_nl<T, 1, ROW_MATVEC>(items, n, blocks, smem, s);
-    if (NL == 2) return launch_row_batch_nl<T, 2, ROW_MATVEC>(items, n, blocks, smem, s);
-    if (NL == 3) return launch_row_batch_nl<T, 3, ROW_MATVEC>(items, n, blocks, smem, s);
+    if (NL == 1) return launch_row_batch_nl<T, 1, ROW_MATVEC>(items, n, blocks, smem, threads, s);
+    if (NL == 2) return launch_row_batch_nl<T, 2, ROW_MATVEC>(items, n, blocks, smem, threads, s);
+    if (NL == 3) return launch_row_batch_nl<T, 3, ROW_MATVEC>(items, n, blocks, smem, threads, s);
   } else if constexpr (sizeof(T) == 8) {
-    if (mode == ROW_TOREAL && NL == 1) return launch_row_batch_nl<T, 1, ROW_TOREAL>(items, n, blocks, smem, s);
+    if (mode == ROW_TOREAL && NL == 1) return launch_row_batch_nl<T, 1, ROW_TOREAL>(items, n, blocks, smem, threads, s);
     if (mode == ROW_ENERGY) {
       switch (NL) {
-        case 1: return launch_row_batch_nl<T, 1, ROW_ENERGY>(items, n, blocks, smem, s);
-        case 2: return launch_row_batch_nl<T, 2, ROW_ENERGY>(items, n, blocks, smem, s);
-        case 3: return launch_row_batch_nl<T, 3, ROW_ENERGY>(items, n, blocks, smem, s);
-        case 4: return launch_row_batch_nl<T, 4, ROW_ENERGY>(items, n, blocks, smem, s);
-        case 5: return launch_row_batch_nl<T, 5, ROW_ENERGY>(items, n, blocks, smem, s);
+        case 1: return launch_row_batch_nl<T, 1, ROW_ENERGY>(items, n, blocks, smem, threads, s);
+        case 2: return launch_row_batch_nl<T, 2, ROW_ENERGY>(items, n, blocks, smem, threads, s);
+        case 3: return launch_row_batch_nl<T, 3, ROW_ENERGY>(items, n, blocks, smem, threads, s);
+        case 4: return launch_row_batch_nl<T, 4, ROW_ENERGY>(items, n, blocks, smem, threads, s);
+        case 5: return launch_row_batch_nl<T, 5, ROW_ENERGY>(items, n, blocks, smem, threads, s);
         default: break;
       }
     }
@@ -189,8 +189,8 @@ ghb_status launch_row_batch(int mode, int NL, const RowItem* items, int n, int64
   set_error("internal: unsupported batched row pass");
   return GHB_ERR_INVALID;
 }
-template ghb_status launch_row_batch<double>(int, int, const RowItem*, int, int64_t, size_t, cudaStream_t);
-template ghb_status launch_row_batch<float>(int, int, const RowItem*, int, int64_t, size_t, cudaStream_t);
+template ghb_status launch_row_batch<double>(int, int, const RowItem*, int, int64_t, size_t, int, cudaStream_t);
+template ghb_status launch_row_batch<float>(int, int, const RowItem*, int, int64_t, size_t, int, cudaStream_t);
 
 template <typename T>
 ghb_status launch_row(int mode, const RowArgs& a, const FftPlan& pl, cudaStream_t s) {

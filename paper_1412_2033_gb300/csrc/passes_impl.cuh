@@ -18,6 +18,7 @@
 // precision and tile-width group) so that the library compiles in parallel.
 #pragma once
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <mutex>
@@ -70,14 +71,40 @@ __device__ __forceinline__ int bix(int i) {
   else return pidx<C>(i);
 }
 
-// Threads of a column-pass CTA.
-// FP64 size-specialised transforms hold a radix group of up to 27 complex
-// doubles per thread, which needs more than the 128 registers a 512-thread CTA
-// allows.
+// Butterflies of one line in the pass with the fewest (the size-specialised
+// plan of length M): a CTA of the last-axis pass keeps all its threads busy
+// only if its interleaved lines times this count reach its thread count.
+template <int M>
+__host__ __device__ constexpr int ct_min_units() {
+  constexpr CtPlan P = ct_plan(M);
+  int mn = M;
+  for (int i = 0; i < P.npass; ++i) {
+    const int u = M / (P.ra[i] * P.rb[i] * P.rc[i]);
+    if (u < mn) mn = u;
+  }
+  return mn;
+}
+// Threads of a column-pass CTA.  Runtime plans: 512 (FP32) or 256 (FP64).
+// Size-specialised transforms: one thread per butterfly of the pass with the
+// fewest (TW lines of ct_min_units each), in whole warps, between 128 and 512
+// (FP32) or 256 (FP64) -- FP64 holds a radix group of up to 27 complex
+// doubles per thread, which needs more than the 128 registers a 512-thread
+// CTA allows.  col_min_blocks keeps the register budget of a full block.
 template <typename T, int TW, int MCT>
 __host__ __device__ constexpr int col_threads() {
-  if constexpr (MCT != 0) return (sizeof(T) == 4 && MCT * TW >= 2048) ? 512 : 256;
-  else return sizeof(T) == 8 ? 256 : 512;
+  if constexpr (MCT != 0) {
+    constexpr int full = sizeof(T) == 4 ? 512 : 256;
+    int t = ((ct_min_units<MCT>() * TW + 31) / 32) * 32;
+    if (t < 128) t = 128;
+    return t < full ? t : full;
+  } else {
+    return sizeof(T) == 8 ? 256 : 512;
+  }
+}
+template <typename T, int TW, int MCT>
+__host__ __device__ constexpr int col_min_blocks() {
+  constexpr int full = sizeof(T) == 4 ? 512 : 256;
+  return (full + col_threads<T, TW, MCT>() - 1) / col_threads<T, TW, MCT>();
 }
 
 // ---------------------------------------------------------------------------
@@ -87,23 +114,24 @@ __host__ __device__ constexpr int col_threads() {
 // line t is input row i(n) = n + half (n <= half) or n - M + half
 // (n >= M - half), zero in between; with UPDATE the entry is r + beta p_old
 // and is written back to p_new once all of a unit's entries are loaded.
-// The pointers are offset to (row half, column j0) of the tile, so an entry's
-// offset |r| inner + t stays within one component's field and fits 32 bits
-// (a 64-bit index per loaded entry would hold two registers each until the
-// write-back).
+// off[t] is the element offset of row 0 of line t's column (a tile's lines
+// may belong to different outer indices); offsets are 32-bit (the launcher
+// rejects operands of 2^31 entries or more), which keeps a unit's indices in
+// one register each until the write-back.
 template <typename C, typename T, bool UPDATE>
 struct ColSource {
   static constexpr bool kWriteBack = UPDATE;
   const C* __restrict__ in;
   const C* __restrict__ pold;
   C* __restrict__ pnew;
+  const int* off;
   T beta;
   int inner;        // row stride
   int half, M, width;
   __device__ __forceinline__ int index(int t, int n, bool& ok) const {
     const int r = n <= half ? n : (n >= M - half ? n - M : M);   // row offset from the centre
     ok = r != M && t < width;
-    return r * inner + t;
+    return off[t] + (r + half) * inner;
   }
   __device__ __forceinline__ C operator()(int t, int n) const {
     bool ok;
@@ -135,10 +163,28 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
   const int npass = load_passes<C>(st, pl);
 
   const int M = MCT != 0 ? MCT : pl.M;
+  // runtime plans: tile (o, j0 .. j0 + TW) of one outer index; size-specialised
+  // transforms: TW consecutive columns of the flattened (outer, inner) range,
+  // so that no CTA is spent on the ragged end of each outer index
   const int64_t tiles = (a.inner + TW - 1) / TW;
-  const int64_t o = bid / tiles;
-  const int64_t j0 = (bid % tiles) * TW;
-  const int width = static_cast<int>(a.inner - j0 < TW ? a.inner - j0 : TW);
+  const int64_t o = MCT != 0 ? 0 : bid / tiles;
+  const int64_t j0 = MCT != 0 ? 0 : (bid % tiles) * TW;
+  int width = static_cast<int>(a.inner - j0 < TW ? a.inner - j0 : TW);
+  __shared__ int s_in[MCT != 0 ? TW : 1], s_out[MCT != 0 ? TW : 1];
+  if constexpr (MCT != 0) {
+    const int64_t ncols = a.outer * a.inner;
+    const int64_t g0 = bid * TW;
+    width = static_cast<int>(ncols - g0 < TW ? ncols - g0 : TW);
+    const int64_t rows_in = SIGN > 0 ? a.Lin : M;
+    const int64_t rows_out = SIGN > 0 ? M : a.Lout;
+    if (threadIdx.x < TW) {
+      const int64_t g = g0 + (static_cast<int>(threadIdx.x) < width ? threadIdx.x : width - 1);
+      const int64_t oo = g / a.inner, jj = g - oo * a.inner;
+      s_in[threadIdx.x] = static_cast<int>(oo * rows_in * a.inner + jj);
+      s_out[threadIdx.x] = static_cast<int>(oo * rows_out * a.inner + jj);
+    }
+    __syncthreads();
+  }
   const C* __restrict__ tw = twtab<C>(pl);
   const int* __restrict__ perm = MCT != 0 ? pl.perm_ct : pl.perm;
 
@@ -152,21 +198,19 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
     const int half = (Lin - 1) / 2;
     T beta = T(0);
     if constexpr (MODE == COL_PUPDATE) beta = static_cast<T>(a.st->beta);
-    const int64_t base = (o * Lin + half) * a.inner + j0;   // (row half, column j0) of this tile
     const C* pold = nullptr;
     C* pnew = nullptr;
     if constexpr (MODE == COL_PUPDATE) {
-      pold = static_cast<const C*>(a.pold) + base;
-      pnew = static_cast<C*>(a.pnew) + base;
+      pold = static_cast<const C*>(a.pold);
+      pnew = static_cast<C*>(a.pnew);
     }
-    ColSource<C, T, MODE == COL_PUPDATE> src{in + base, pold, pnew, beta, static_cast<int>(a.inner), half, M,
-                                            width};
+    ColSource<C, T, MODE == COL_PUPDATE> src{in, pold, pnew, s_in, beta, static_cast<int>(a.inner), half, M, width};
     fft_dit_ct_src<+1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, src);
     C* __restrict__ out = static_cast<C*>(a.out);
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
       const int t = u % TW;
       const int m = u / TW;
-      if (t < width) out[(o * M + m) * a.inner + j0 + t] = buf[m * TW + t];
+      if (t < width) out[s_out[t] + m * static_cast<int>(a.inner)] = buf[m * TW + t];
     }
   } else if constexpr (MCT != 0) {
     // forward, size-specialised: natural-order input copied in, the last
@@ -175,7 +219,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
       const int t = u % TW;
       const int m = u / TW;
-      if (t < width) cp_async<sizeof(C)>(buf + u, in + (o * M + m) * a.inner + j0 + t);
+      if (t < width) cp_async<sizeof(C)>(buf + u, in + (s_in[t] + m * static_cast<int>(a.inner)));
       else buf[u] = mk(T(0), T(0));
     }
     cp_async_commit();
@@ -187,7 +231,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
     const T inv = T(1) / T(M);
     auto snk = [&](int t, int n, C v) {
       const int i = n <= half ? n + half : (n >= M - half ? n - M + half : -1);
-      if (i >= 0 && t < width) out[(o * Lout + i) * a.inner + j0 + t] = inv * v;
+      if (i >= 0 && t < width) out[s_out[t] + i * static_cast<int>(a.inner)] = inv * v;
     };
     fft_dif_ct_snk<-1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, snk);
   } else if (SIGN > 0) {
@@ -291,7 +335,7 @@ constexpr int kColThreads32 = 512;
 constexpr int kColThreads64 = 256;
 
 template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
-__global__ void __launch_bounds__(col_threads<T, TW, MCT>())
+__global__ void __launch_bounds__(col_threads<T, TW, MCT>(), col_min_blocks<T, TW, MCT>())
     col_kernel(ColArgs a, FftPlan pl) {
   col_body<T, TW, SIGN, MODE, MCT>(a, pl, blockIdx.x);
 }
@@ -327,7 +371,11 @@ inline ghb_status launch_col_t(const ColArgs& a, const FftPlan& pl, cudaStream_t
   static std::atomic<unsigned long long> attr_mask{0};
   TRY_STATUS(ensure_dyn_smem(col_kernel<T, TW, SIGN, MODE, MCT>, 220 * 1024, attr_mask));
   const int64_t tiles = (a.inner + TW - 1) / TW;
-  const int64_t grid = tiles * a.outer;
+  const int64_t grid = MCT != 0 ? (a.outer * a.inner + TW - 1) / TW : tiles * a.outer;
+  if (MCT != 0 && a.outer * std::max<int64_t>(std::max<int64_t>(a.Lin, a.Lout), pl.M) * a.inner >= (int64_t(1) << 31)) {
+    set_error("column pass operand of 2^31 entries or more");
+    return GHB_ERR_INVALID;
+  }
   const int threads = MCT != 0 ? col_threads<T, TW, MCT>()
                                : ((sizeof(T) == 4 && pl.M * TW >= 2048) ? kColThreads32 : 256);
   col_kernel<T, TW, SIGN, MODE, MCT><<<static_cast<unsigned>(grid), threads, smem, s>>>(a, pl);
@@ -345,23 +393,26 @@ ghb_status launch_col_tw(int sign, int mode, const ColArgs& a, const FftPlan& pl
 }
 
 template <typename T, int TW, int SIGN, int MODE>
-inline ghb_status launch_col_batch_t(const ColItem* items, int n, int64_t blocks, size_t smem,
+inline ghb_status launch_col_batch_t(const ColItem* items, int n, int64_t blocks, size_t smem, int threads,
                                      cudaStream_t s) {
   static std::atomic<unsigned long long> attr_mask{0};
   TRY_STATUS(ensure_dyn_smem(col_kernel_batch<T, TW, SIGN, MODE>, 220 * 1024, attr_mask));
-  const int threads = sizeof(T) == 4 ? kColThreads32 : kColThreads64;
-  col_kernel_batch<T, TW, SIGN, MODE><<<static_cast<unsigned>(blocks), threads, smem, s>>>(items, n);
+  // threads <= 0: the kernel's full block; fewer for short transforms, whose
+  // passes have fewer butterflies than a full block has threads
+  const int full = sizeof(T) == 4 ? kColThreads32 : kColThreads64;
+  const int nt = (threads > 0 && threads < full) ? threads : full;
+  col_kernel_batch<T, TW, SIGN, MODE><<<static_cast<unsigned>(blocks), nt, smem, s>>>(items, n);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }
 
 template <typename T, int TW>
-ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, int64_t blocks, size_t smem,
+ghb_status launch_col_batch_tw(int sign, int mode, const ColItem* items, int n, int64_t blocks, size_t smem, int threads,
                                cudaStream_t s) {
   if (sign > 0)
-    return mode == COL_PUPDATE ? launch_col_batch_t<T, TW, +1, COL_PUPDATE>(items, n, blocks, smem, s)
-                               : launch_col_batch_t<T, TW, +1, COL_PLAIN>(items, n, blocks, smem, s);
-  return launch_col_batch_t<T, TW, -1, COL_PLAIN>(items, n, blocks, smem, s);
+    return mode == COL_PUPDATE ? launch_col_batch_t<T, TW, +1, COL_PUPDATE>(items, n, blocks, smem, threads, s)
+                               : launch_col_batch_t<T, TW, +1, COL_PLAIN>(items, n, blocks, smem, threads, s);
+  return launch_col_batch_t<T, TW, -1, COL_PLAIN>(items, n, blocks, smem, threads, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -534,7 +585,8 @@ constexpr int kRowThreads = 256;
 // instead of staging it, which frees shared memory for a fourth CTA per SM,
 // and run 192 threads per CTA (a radix-27 pass at M = 4374 has 162
 // butterflies per line).  At M = 4374: 173 us per launch against 184 us with
-// the staged A_M and 256 threads.
+// the staged A_M and 256 threads; at M = 270 (15 lines per CTA): 300 us
+// against 334 us.
 template <typename T, int MCT>
 __host__ __device__ constexpr bool row_streams_multiplier() {
   return MCT != 0 && sizeof(T) == 4;
@@ -571,7 +623,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
   using C = typename CT<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassSmem st;
-  __shared__ LineDesc ld[2 * NL];
+  __shared__ LineDesc ld[2 * NL], ldn[2 * NL];   // this group's lines, the next group's
   if (a.st != nullptr && a.st->done != RUNNING) return;
   const int npass = load_passes<C>(st, pl);
 
@@ -595,13 +647,35 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     d.valid = (rho < nrl) && (d.row < a.rows);
     return d;
   };
-  auto issue_spectra = [&](int64_t grp) {
-#pragma unroll
-    for (int rho = 0; rho < 2 * NL; ++rho) {
-      const LineDesc d = desc(grp, rho);
-      if (!d.valid) continue;
-      const C* src = static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H;
-      for (int k = threadIdx.x; k < H; k += blockDim.x) cp_async<sizeof(C)>(sin + rho * H + k, src + k);
+  // Copies of the half spectra of the lines described by L[0 .. 2NL) into the
+  // staging area.  Long rows (H >= the block): line by line, the block
+  // striding over k.  Short rows: one flat loop over (line, k), the line and k
+  // of a thread advanced by the block size each step (no division per entry).
+  auto issue_from = [&](const LineDesc* L) {
+    if (H >= static_cast<int>(blockDim.x)) {
+#pragma unroll 1
+      for (int rho = 0; rho < 2 * NL; ++rho) {
+        const LineDesc d = L[rho];
+        if (!d.valid) continue;
+        const C* src = static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H;
+        for (int k = threadIdx.x; k < H; k += blockDim.x) cp_async<sizeof(C)>(sin + rho * H + k, src + k);
+      }
+      return;
+    }
+    const int step_r = static_cast<int>(blockDim.x) / H, step_k = static_cast<int>(blockDim.x) - step_r * H;
+    int rho = static_cast<int>(threadIdx.x) / H;
+    int k = static_cast<int>(threadIdx.x) - rho * H;
+    while (rho < 2 * NL) {
+      const LineDesc d = L[rho];
+      if (d.valid)
+        cp_async<sizeof(C)>(sin + rho * H + k,
+                            static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H + k);
+      rho += step_r;
+      k += step_k;
+      if (k >= H) {
+        k -= H;
+        ++rho;
+      }
     }
   };
   auto issue_multiplier = [&](int64_t grp) {
@@ -615,13 +689,20 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
 
   int64_t grp = bid;
   if (grp < groups) {
-    issue_spectra(grp);
+    if (threadIdx.x < 2 * NL) ldn[threadIdx.x] = desc(grp, threadIdx.x);
+    __syncthreads();
+    issue_from(ldn);
     cp_async_commit();
     issue_multiplier(grp);
     cp_async_commit();
+    __syncthreads();   // ldn is rewritten at the top of the loop
   }
   for (; grp < groups; grp += nb) {
-    if (threadIdx.x < 2 * NL) ld[threadIdx.x] = desc(grp, threadIdx.x);
+    // every thread has issued the copies of ldn's lines (barriers since then)
+    if (threadIdx.x < 2 * NL) {
+      ld[threadIdx.x] = desc(grp, threadIdx.x);
+      ldn[threadIdx.x] = desc(grp + nb, threadIdx.x);
+    }
     cp_async_wait<1>();          // spectra(g) are in; A_M(g) may still be in flight
     __syncthreads();
 
@@ -652,7 +733,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
         return mk(a0 * z.x, a1 * z.y);
       };
       auto after_first = [&]() {   // the staged spectra are read: stage the next group's
-        if (grp + nb < groups) issue_spectra(grp + nb);
+        if (grp + nb < groups) issue_from(ldn);
         cp_async_commit();
       };
       auto before_fused = [&]() {  // A_M(g) is in; spectra(g+1) may still be in flight
@@ -680,7 +761,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
       buf[bix<MCT, C>(__ldg(&perm[k]) * NL + j)] = mk(T(0), T(0));
     }
     __syncthreads();
-    if (grp + nb < groups) issue_spectra(grp + nb);   // staging is free again
+    if (grp + nb < groups) issue_from(ldn);   // staging is free again
     fft_dit<+1, NL>(buf, st, npass, M, tw);
     cp_async_commit();
 
@@ -742,11 +823,12 @@ __global__ void __launch_bounds__(kRowThreads, sizeof(T) == 4 ? 3 : 1)
 }
 
 template <typename T, int NL, int MODE>
-inline ghb_status launch_row_batch_t(const RowItem* items, int n, int64_t blocks, size_t smem,
+inline ghb_status launch_row_batch_t(const RowItem* items, int n, int64_t blocks, size_t smem, int threads,
                                      cudaStream_t s) {
   static std::atomic<unsigned long long> attr_mask{0};
   TRY_STATUS(ensure_dyn_smem(row_kernel_batch<T, NL, MODE>, 200 * 1024, attr_mask));
-  row_kernel_batch<T, NL, MODE><<<static_cast<unsigned>(blocks), kRowThreads, smem, s>>>(items, n);
+  const int nt = (MODE == ROW_MATVEC && threads > 0 && threads < kRowThreads) ? threads : kRowThreads;
+  row_kernel_batch<T, NL, MODE><<<static_cast<unsigned>(blocks), nt, smem, s>>>(items, n);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }
@@ -816,8 +898,39 @@ ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& 
   constexpr int TW = col_tile_width(M, 2 * sizeof(T));
   return launch_col_tw<T, TW, M>(sign, mode, a, pl, s);
 }
+// Interleaved complex lines that give every thread a butterfly in every pass,
+// for PER_ROW real lines per row (2 in 2-D, 3 in 3-D: a multiple of 3 so that
+// the lines make whole rows), at most 32.
+template <typename T, int M, int PER_ROW>
+__host__ __device__ constexpr int ct_fill_lines() {
+  constexpr int thr = row_threads<T, M>();
+  int nl = (thr + ct_min_units<M>() - 1) / ct_min_units<M>();
+  if (nl > 32) nl = 32;
+  if (PER_ROW == 3) nl = 3 * ((nl + 2) / 3);
+  if (nl > 32) nl = 30;
+  return nl;
+}
+
 template <typename T, int M>
 ghb_status launch_row_ct_m(int NL, const RowArgs& a, const FftPlan& pl, int rows_per_cta, cudaStream_t s) {
+  // Short transforms (the 3-D double grids, 2-D ones up to M = 486) leave
+  // most threads without a butterfly at one to three lines per CTA: take as
+  // many rows as fill the CTA when the row rule leaves more than half of the
+  // threads idle and the staging still fits (at M = 1458, where two lines
+  // leave 44 % idle, four lines measured slower: 32.7 against 28.4 us).
+  const int per_row = a.nfields * a.ncomp;
+  constexpr int thr = row_threads<T, M>();
+  if ((per_row == 2 || per_row == 3) && ct_min_units<M>() * NL * 2 < thr) {
+    constexpr int NL2 = ct_fill_lines<T, M, 2>(), NL3 = ct_fill_lines<T, M, 3>();
+    const int want = per_row == 2 ? NL2 : NL3;
+    const int rows = 2 * want / per_row;
+    const int arows = row_streams_multiplier<T, M>() ? 0 : rows;
+    const size_t smem = per_row == 2 ? row_staged_smem<T, NL2>(M, a.H, arows) : row_staged_smem<T, NL3>(M, a.H, arows);
+    if (want > NL && smem <= 200 * 1024) {
+      if (per_row == 2) return launch_row_t<T, NL2, ROW_MATVEC, M>(a, pl, rows, s);
+      return launch_row_t<T, NL3, ROW_MATVEC, M>(a, pl, rows, s);
+    }
+  }
   switch (NL) {
     case 1: return launch_row_t<T, 1, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
     case 2: return launch_row_t<T, 2, ROW_MATVEC, M>(a, pl, rows_per_cta, s);
