@@ -610,10 +610,20 @@ __host__ __device__ constexpr int row_threads() {
 // wait_group 1 therefore waits for A_M(g) alone.  Kernels that stream A_M
 // (row_streams_multiplier) have no A_M area and commit empty A_M groups, so the
 // count is the same.
+// Staged half spectra: the two real lines of complex line j side by side,
+// entry (j, k) at pair index j * row_pair_stride(H) + k (an odd stride, so that
+// threads of consecutive lines reading the same k fall on different banks).
+__host__ __device__ inline int row_pair_stride(int H) { return H | 1; }
+template <typename T>
+__host__ __device__ inline size_t row_buf_elems(int M, int NL) {   // rounded to 16 bytes
+  using C = typename CT<T>::type;
+  const size_t e = padded_elems<C>(static_cast<size_t>(M) * NL);
+  return sizeof(C) >= 16 ? e : (e + 1) & ~static_cast<size_t>(1);
+}
 template <typename T, int NL>
 __host__ __device__ inline size_t row_staged_smem(int M, int H, int rows_per_cta) {
   using C = typename CT<T>::type;
-  return padded_elems<C>(static_cast<size_t>(M) * NL) * sizeof(C) + static_cast<size_t>(2 * NL) * H * sizeof(C) +
+  return row_buf_elems<T>(M, NL) * sizeof(C) + static_cast<size_t>(2 * NL) * row_pair_stride(H) * sizeof(C) +
          static_cast<size_t>(rows_per_cta) * M * sizeof(T);
 }
 
@@ -624,6 +634,10 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassSmem st;
   __shared__ LineDesc ld[2 * NL], ldn[2 * NL];   // this group's lines, the next group's
+  // per complex line j of this group: bit 0 / bit 1 = real line 2j / 2j+1 is
+  // valid; offsets of their A_M rows (in `am`, or in the staged rows `sa`)
+  __shared__ int lmask[NL];
+  __shared__ int2 lrow[NL];
   if (a.st != nullptr && a.st->done != RUNNING) return;
   const int npass = load_passes<C>(st, pl);
 
@@ -633,8 +647,13 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
   const int nrl = rows_per_cta * per_row;
   const int64_t groups = (a.rows + rows_per_cta - 1) / rows_per_cta;
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* sin = buf + padded_elems<C>(static_cast<size_t>(M) * NL);
-  T* sa = reinterpret_cast<T*>(sin + 2 * NL * H);
+  C* sin = buf + row_buf_elems<T>(M, NL);
+  const int SH = row_pair_stride(H);
+  T* sa = reinterpret_cast<T*>(sin + 2 * NL * SH);
+  struct alignas(sizeof(C) >= 16 ? 16 : 2 * sizeof(C)) Pair {
+    C a, b;
+  };
+  const Pair* spair = reinterpret_cast<const Pair*>(sin);
   const C* __restrict__ tw = twtab<C>(pl);
   const int* __restrict__ perm = MCT != 0 ? pl.perm_ct : pl.perm;
   const T* __restrict__ am = static_cast<const T*>(a.a);
@@ -658,7 +677,8 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
         const LineDesc d = L[rho];
         if (!d.valid) continue;
         const C* src = static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H;
-        for (int k = threadIdx.x; k < H; k += blockDim.x) cp_async<sizeof(C)>(sin + rho * H + k, src + k);
+        C* dst = sin + (rho >> 1) * 2 * SH + (rho & 1);
+        for (int k = threadIdx.x; k < H; k += blockDim.x) cp_async<sizeof(C)>(dst + 2 * k, src + k);
       }
       return;
     }
@@ -668,7 +688,7 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     while (rho < 2 * NL) {
       const LineDesc d = L[rho];
       if (d.valid)
-        cp_async<sizeof(C)>(sin + rho * H + k,
+        cp_async<sizeof(C)>(sin + ((rho >> 1) * SH + k) * 2 + (rho & 1),
                             static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H + k);
       rho += step_r;
       k += step_k;
@@ -703,6 +723,15 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
       ld[threadIdx.x] = desc(grp, threadIdx.x);
       ldn[threadIdx.x] = desc(grp + nb, threadIdx.x);
     }
+    if (threadIdx.x < NL) {
+      const int j = threadIdx.x;
+      const LineDesc d0 = desc(grp, 2 * j), d1 = desc(grp, 2 * j + 1);
+      lmask[j] = (d0.valid ? 1 : 0) | (d1.valid ? 2 : 0);
+      if constexpr (row_streams_multiplier<T, MCT>())
+        lrow[j] = make_int2(d0.valid ? static_cast<int>(d0.row * M) : 0, d1.valid ? static_cast<int>(d1.row * M) : 0);
+      else
+        lrow[j] = make_int2(((2 * j) / per_row) * M, ((2 * j + 1) / per_row) * M);
+    }
     cp_async_wait<1>();          // spectra(g) are in; A_M(g) may still be in flight
     __syncthreads();
 
@@ -716,19 +745,27 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
         const bool lo = n < H, hi = n > M - H;
         const int k = lo ? n : M - n;
         C A = mk(T(0), T(0)), B = mk(T(0), T(0));
-        if ((lo || hi) && ld[2 * j].valid) A = sin[(2 * j) * H + k];
-        if ((lo || hi) && ld[2 * j + 1].valid) B = sin[(2 * j + 1) * H + k];
+        if (lo || hi) {
+          // both real lines in one load; a line that is not valid this group
+          // holds stale entries, which the mask drops
+          const Pair v = spair[j * SH + k];
+          const int msk = lmask[j];
+          if (msk & 1) A = v.a;
+          if (msk & 2) B = v.b;
+        }
         return lo ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
       };
       // multiply by A_M between the transforms, in registers
       auto mul = [&](int j, int m, C z) -> C {
         T a0 = T(0), a1 = T(0);
+        const int msk = lmask[j];
+        const int2 ro = lrow[j];
         if constexpr (row_streams_multiplier<T, MCT>()) {
-          if (ld[2 * j].valid) a0 = __ldg(&am[ld[2 * j].row * M + m]);
-          if (ld[2 * j + 1].valid) a1 = __ldg(&am[ld[2 * j + 1].row * M + m]);
+          if (msk & 1) a0 = __ldg(&am[ro.x + m]);
+          if (msk & 2) a1 = __ldg(&am[ro.y + m]);
         } else {
-          if (ld[2 * j].valid) a0 = sa[((2 * j) / per_row) * M + m];
-          if (ld[2 * j + 1].valid) a1 = sa[((2 * j + 1) / per_row) * M + m];
+          if (msk & 1) a0 = sa[ro.x + m];
+          if (msk & 2) a1 = sa[ro.y + m];
         }
         return mk(a0 * z.x, a1 * z.y);
       };
@@ -750,8 +787,10 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     for (int u = threadIdx.x; u < NL * H; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
       const int k = (NL == 1) ? u : u / NL;
-      const C A = ld[2 * j].valid ? sin[(2 * j) * H + k] : mk(T(0), T(0));
-      const C B = ld[2 * j + 1].valid ? sin[(2 * j + 1) * H + k] : mk(T(0), T(0));
+      const Pair v = spair[j * SH + k];
+      const int msk = lmask[j];
+      const C A = (msk & 1) ? v.a : mk(T(0), T(0));
+      const C B = (msk & 2) ? v.b : mk(T(0), T(0));
       buf[bix<MCT, C>(__ldg(&perm[k]) * NL + j)] = mk(A.x - B.y, A.y + B.x);
       if (k > 0) buf[bix<MCT, C>(__ldg(&perm[M - k]) * NL + j)] = mk(A.x + B.y, B.x - A.y);
     }
@@ -770,10 +809,11 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     for (int u = threadIdx.x; u < NL * M; u += blockDim.x) {
       const int j = (NL == 1) ? 0 : u % NL;
       const int m = (NL == 1) ? u : u / NL;
-      const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
+      const int msk = lmask[j];
+      const int2 ro = lrow[j];
       const C z = buf[bix<MCT, C>(m * NL + j)];
-      const T a0 = d0.valid ? sa[((2 * j) / per_row) * M + m] : T(0);
-      const T a1 = d1.valid ? sa[((2 * j + 1) / per_row) * M + m] : T(0);
+      const T a0 = (msk & 1) ? sa[ro.x + m] : T(0);
+      const T a1 = (msk & 2) ? sa[ro.y + m] : T(0);
       buf[bix<MCT, C>(m * NL + j)] = mk(a0 * z.x, a1 * z.y);
     }
     __syncthreads();
