@@ -72,7 +72,7 @@ def parse():
                     help="arrival window before the measured one (its requests are not counted)")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="sustained arrival rate as a fraction of the measured service capacity")
-    ap.add_argument("--serve-probe", type=int, default=48,
+    ap.add_argument("--serve-probe", type=int, default=96,
                     help="requests of the closed-loop capacity probe (mixed; a quarter of it for FP64)")
     ap.add_argument("--serve-overload-rate", type=float, default=200.0,
                     help="arrival rate of the short overload run (0 = skip)")

@@ -291,6 +291,12 @@ ghb_status ghb_profile_read(ghb_ctx* ctx, int cls, int64_t* launches, double* to
  * fits the batch's budget, so requests submitted while others run join the
  * running work at the next step (continuous batching); finished requests leave
  * and free their memory.  A batch owns its CUDA stream and device memory.
+ * Requests of at least 2^22 double-grid points (d = 3 from M = 162, d = 2 from
+ * M = 2048) are solved instead by two worker threads of the batch, each with a
+ * private context on its own stream, while the batched cycles run (a
+ * large solve would otherwise set the pace of every batched iteration); their
+ * results enter the same queue, and the context's memory counts against the
+ * budget while it exists.
  * ------------------------------------------------------------------------ */
 typedef struct ghb_batch ghb_batch;
 
@@ -331,7 +337,8 @@ int ghb_batch_results(ghb_batch* b, ghb_result* out, int max_results);
 ghb_status ghb_batch_stats(const ghb_batch* b, int64_t* bytes_in_use, int* active, int* pending,
                            int64_t* finished, int64_t* launches);
 
-/* Release the batch (pending and running requests are dropped).  NULL is a no-op. */
+/* Release the batch (pending and running requests are dropped; large requests
+ * in progress in the workers finish first).  NULL is a no-op. */
 void ghb_batch_destroy(ghb_batch* b);
 
 /* ghb_gram without any device allocation (the paper has no counterpart; this

@@ -20,14 +20,29 @@
 //             their results become available and their memory returns to the pool.
 // Requests submitted while others run are admitted at the next cycle, so work
 // of requests of different ages overlaps on the device (continuous batching).
+//
+// Large requests (at least kLargeGrid double-grid points) do not enter the
+// batched cycles: every batched launch advances all active solves together,
+// so one large solve would set the pace of every iteration for all the small
+// ones.  A worker thread solves them one at a time with a private context
+// (ghb_create / ghb_bounds on the context's own stream: size-specialised,
+// autotuned kernels) while the cycles run, two at a time; their results join
+// the same queue.
+// The context's device memory counts against the batch's budget while it
+// exists.  Context set-up and teardown (which allocate and copy synchronously)
+// never overlap the capture of a cycle's CUDA graph.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ghb_internal.cuh"
@@ -164,11 +179,34 @@ struct Launch {
 
 }  // namespace
 
+// Double-grid points from which a request is solved by the large-request
+// worker instead of the batched cycles (2^22: d = 3 from M = 162, d = 2 from
+// M = 2048).
+constexpr int64_t kLargeGrid = int64_t(1) << 22;
+
+// Large requests solved at the same time (each by its own worker thread and
+// context): two, so that one solve's launch gaps and barrier waits are filled
+// by the other's kernels.
+constexpr int kLaneWorkers = 2;
+
+struct LargeLane {
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request> queue;
+  std::deque<ghb_result> done;
+  bool stop = false;
+  int running = 0;
+  int device = 0;
+};
+
 struct ghb_batch {
   ghb_options opt{};
   cudaStream_t stream = nullptr;
   int64_t budget = 0;
-  int64_t in_use = 0;
+  std::atomic<int64_t> in_use{0};
+  LargeLane lane;
+  std::mutex capture_mu;   // held while a cycle's graph is captured
   int max_active = 0;
   int64_t next_id = 1;
   std::map<int, PlanEntry> plans;
@@ -762,6 +800,7 @@ ghb_status iterate(ghb_batch* b, int K) {
     b->graph = nullptr;
   }
   cudaGraph_t g = nullptr;
+  std::lock_guard<std::mutex> capture_lock(b->capture_mu);
   GHB_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
   ghb_status st = GHB_OK;
   for (const Launch& l : L) {
@@ -993,6 +1032,72 @@ ghb_status retire(ghb_batch* b) {
 
 }  // namespace
 
+// A large-request worker: one request at a time through a private context.
+void lane_main(ghb_batch* b) {
+  LargeLane& ln = b->lane;
+  cudaSetDevice(ln.device);
+  for (;;) {
+    Request rq;
+    {
+      std::unique_lock<std::mutex> lk(ln.mu);
+      ln.cv.wait(lk, [&] { return ln.stop || !ln.queue.empty(); });
+      if (ln.stop) return;
+      rq = std::move(ln.queue.front());
+      ln.queue.pop_front();
+      ++ln.running;
+    }
+    ghb_result r{};
+    r.id = rq.id;
+    r.d = rq.d;
+    const double t_start = now_s();
+    ghb_ctx* c = nullptr;
+    ghb_status st;
+    {
+      std::lock_guard<std::mutex> g(b->capture_mu);
+      st = ghb_create(&c, rq.d, rq.N, rq.a0, rq.phases.empty() ? nullptr : rq.phases.data(),
+                      static_cast<int>(rq.phases.size()), &b->opt);
+    }
+    if (st == GHB_OK) {
+      const int64_t bytes = ghb_device_bytes(c);
+      b->in_use += bytes;
+      st = ghb_bounds(c, r.upper, r.lower, r.info);
+      {
+        std::lock_guard<std::mutex> g(b->capture_mu);
+        ghb_destroy(c);
+      }
+      b->in_use -= bytes;
+    }
+    r.status = st;
+    r.seconds_queued = t_start - rq.t_submit;
+    r.seconds_total = now_s() - rq.t_submit;
+    {
+      std::lock_guard<std::mutex> lk(ln.mu);
+      ln.done.push_back(r);
+      --ln.running;
+    }
+    ln.cv.notify_all();
+  }
+}
+
+// Results of the worker into the batch's queue; with `wait`, block up to 50 ms
+// for one while the worker is busy.
+void drain_lane(ghb_batch* b, bool wait) {
+  LargeLane& ln = b->lane;
+  std::unique_lock<std::mutex> lk(ln.mu);
+  if (wait && ln.done.empty() && (ln.running || !ln.queue.empty()))
+    ln.cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return !ln.done.empty(); });
+  while (!ln.done.empty()) {
+    b->results.push_back(ln.done.front());
+    ln.done.pop_front();
+    ++b->finished;
+  }
+}
+
+bool lane_busy(ghb_batch* b) {
+  std::lock_guard<std::mutex> lk(b->lane.mu);
+  return b->lane.running || !b->lane.queue.empty() || !b->lane.done.empty();
+}
+
 extern "C" {
 
 ghb_status ghb_batch_create(ghb_batch** out, const ghb_options* opt, int64_t budget_bytes, int max_active) {
@@ -1071,8 +1176,21 @@ ghb_status ghb_batch_submit(ghb_batch* b, int d, const int* N, double a0, const 
   r.a0 = a0;
   r.phases.assign(phases, phases + n_phases);
   r.t_submit = now_s();
-  b->pending.push_back(r);
   if (id_out) *id_out = r.id;
+  if (g.grid >= kLargeGrid) {
+    LargeLane& ln = b->lane;
+    if (ln.workers.empty()) {
+      cudaGetDevice(&ln.device);
+      for (int w = 0; w < kLaneWorkers; ++w) ln.workers.emplace_back(lane_main, b);
+    }
+    {
+      std::lock_guard<std::mutex> lk(ln.mu);
+      ln.queue.push_back(std::move(r));
+    }
+    ln.cv.notify_all();
+    return GHB_OK;
+  }
+  b->pending.push_back(r);
   return GHB_OK;
 }
 
@@ -1084,18 +1202,28 @@ ghb_status ghb_batch_step(ghb_batch* b, int iterations, int* active_out, int* pe
     TRYB(iterate(b, iterations > 0 ? iterations : 8));
     TRYB(correct(b));
     TRYB(retire(b));
+    // with no batched work left, wait briefly for the large-request worker
+    // instead of returning at once to a caller that loops on ghb_batch_step
+    drain_lane(b, b->active.empty() && b->pending.empty());
   } catch (const std::exception& ex) {
     set_error(std::string("internal error: ") + ex.what());
     return GHB_ERR_INVALID;
   }
-  if (active_out) *active_out = static_cast<int>(b->active.size());
-  if (pending_out) *pending_out = static_cast<int>(b->pending.size());
+  int lane_active = 0, lane_pending = 0;
+  {
+    std::lock_guard<std::mutex> lk(b->lane.mu);
+    lane_active = b->lane.running;
+    lane_pending = static_cast<int>(b->lane.queue.size());
+  }
+  if (active_out) *active_out = static_cast<int>(b->active.size()) + lane_active;
+  if (pending_out) *pending_out = static_cast<int>(b->pending.size()) + lane_pending;
   return GHB_OK;
 }
 
 ghb_status ghb_batch_run(ghb_batch* b, int iterations) {
   if (!b) { set_error("batch is NULL"); return GHB_ERR_INVALID; }
-  while (!b->active.empty() || !b->pending.empty()) TRYB(ghb_batch_step(b, iterations, nullptr, nullptr));
+  while (!b->active.empty() || !b->pending.empty() || lane_busy(b))
+    TRYB(ghb_batch_step(b, iterations, nullptr, nullptr));
   return GHB_OK;
 }
 
@@ -1112,9 +1240,16 @@ int ghb_batch_results(ghb_batch* b, ghb_result* out, int max_results) {
 ghb_status ghb_batch_stats(const ghb_batch* b, int64_t* bytes_in_use, int* active, int* pending,
                            int64_t* finished, int64_t* launches) {
   if (!b) { set_error("batch is NULL"); return GHB_ERR_INVALID; }
+  LargeLane& ln = const_cast<ghb_batch*>(b)->lane;
+  int lane_active = 0, lane_pending = 0;
+  {
+    std::lock_guard<std::mutex> lk(ln.mu);
+    lane_active = ln.running;
+    lane_pending = static_cast<int>(ln.queue.size());
+  }
   if (bytes_in_use) *bytes_in_use = b->in_use;
-  if (active) *active = static_cast<int>(b->active.size());
-  if (pending) *pending = static_cast<int>(b->pending.size());
+  if (active) *active = static_cast<int>(b->active.size()) + lane_active;
+  if (pending) *pending = static_cast<int>(b->pending.size()) + lane_pending;
   if (finished) *finished = b->finished;
   if (launches) *launches = b->launches;
   return GHB_OK;
@@ -1122,6 +1257,15 @@ ghb_status ghb_batch_stats(const ghb_batch* b, int64_t* bytes_in_use, int* activ
 
 void ghb_batch_destroy(ghb_batch* b) {
   if (!b) return;
+  if (!b->lane.workers.empty()) {   // requests in progress finish; queued ones are dropped
+    {
+      std::lock_guard<std::mutex> lk(b->lane.mu);
+      b->lane.stop = true;
+      b->lane.queue.clear();
+    }
+    b->lane.cv.notify_all();
+    for (auto& w : b->lane.workers) w.join();
+  }
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (Inst* in : b->active) {

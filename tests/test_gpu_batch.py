@@ -90,3 +90,27 @@ def test_request_larger_than_budget(ghb):
     b.run()
     r = b.results()[0]
     assert r["id"] == rid and r["status"] == 2          # GHB_ERR_OOM
+
+
+def test_large_requests_beside_the_batch(ghb):
+    """A request of at least 2^22 double-grid points (d = 3 at N = 81, M = 162)
+    is solved by the large-request worker with a private context while the
+    small ones run in the batched cycles: its bounds are those of a single
+    context, the small ones' are unchanged, and the batch reports all of them."""
+    big = W.random_sphere_instance(W.BASE_SEED + 61, N=81)
+    small = [W.random_disk_instance(W.BASE_SEED + 62, N=45), W.random_sphere_instance(W.BASE_SEED + 63, N=11)]
+    b = ghb.Batch()
+    ids = [b.submit(small[0]), b.submit(big), b.submit(small[1])]
+    st = b.stats()
+    assert st["pending"] + st["active"] == 3
+    b.run(iterations=8)
+    res = {r["id"]: r for r in b.results()}
+    assert sorted(res) == sorted(ids)
+    assert b.stats()["finished"] == 3
+    b.close()
+    for rid, m in zip(ids, [small[0], big, small[1]]):
+        r = res[rid]
+        assert r["status"] == 0, r
+        U, L, _, _ = ghb.Context.from_microstructure(m, precision="mixed").bounds()
+        tol = 1e-13 if m is big else 1e-9
+        assert rel(r["upper"], U) < tol and rel(r["lower"], L) < tol
