@@ -941,8 +941,20 @@ ghb_status launch_col_ct_m(int sign, int mode, const ColArgs& a, const FftPlan& 
 // Interleaved complex lines that give every thread a butterfly in every pass,
 // for PER_ROW real lines per row (2 in 2-D, 3 in 3-D: a multiple of 3 so that
 // the lines make whole rows), at most 32.
+// In 3-D the counts below were chosen by a sweep of 6 .. 24 lines on GB300
+// (one d = 3 operator application per setting): lines that make each pass
+// about one full round of the block, with four FP32 CTAs per SM, beat the rule
+// (M = 270: 12 lines, 221 against 242 us FP32 and 4.37 against 5.19 ms FP64;
+// M = 162: 18 lines FP32, 55.8 against 61.7 us; M = 135: 12 lines FP32, 24 FP64;
+// M = 72: 18 lines FP32).
 template <typename T, int M, int PER_ROW>
 __host__ __device__ constexpr int ct_fill_lines() {
+  if (PER_ROW == 3) {
+    if (M == 270) return 12;
+    if (M == 162 && sizeof(T) == 4) return 18;
+    if (M == 135) return sizeof(T) == 4 ? 12 : 24;
+    if (M == 72 && sizeof(T) == 4) return 18;
+  }
   constexpr int thr = row_threads<T, M>();
   int nl = (thr + ct_min_units<M>() - 1) / ct_min_units<M>();
   if (nl > 32) nl = 32;
