@@ -410,12 +410,14 @@ def gram_noalloc(d, N, M, grid, fields, stream=None):
         raise ValueError("d must be 2 or 3 with d orders N and d double-grid sizes M")
     if not 1 <= len(fields) <= d:
         raise ValueError(f"between 1 and d = {d} fields are allowed, got {len(fields)}")
-    dev = torch.cuda.current_device()
 
     def check(t, dtype, n, what):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.dtype == dtype
-                and t.is_contiguous() and t.numel() == n):
-            raise ValueError(f"{what} must be a contiguous {dtype} tensor of {n} entries on cuda:{dev}")
+        ok = isinstance(t, torch.Tensor) and t.is_cuda
+        if ok:
+            dev = torch.cuda.current_device()
+            ok = t.device.index == dev and t.dtype == dtype and t.is_contiguous() and t.numel() == n
+        if not ok:
+            raise ValueError(f"{what} must be a contiguous {dtype} tensor of {n} entries on the current CUDA device")
 
     check(grid, torch.float64, int(np.prod([int(m) for m in M])), "grid")
     nf = d * int(np.prod([int(n) for n in N[:-1]])) * ((int(N[-1]) + 1) // 2)

@@ -106,3 +106,21 @@ def test_tune_set_validation_and_size_rules(lib, monkeypatch):
         assert g.tune_get(510) == cfg
     finally:
         g.tune_reset()
+
+
+def test_gram_noalloc_binding_rejects_bad_arguments(lib):
+    """The binding of ghb_gram_noalloc checks its arguments before the call:
+    dimension, field count (1..d) and tensor kind (host tensors, wrong dtype,
+    wrong size) are rejected with ValueError and never reach the library."""
+    torch = pytest.importorskip("torch")
+    import paper_1412_2033_gb300 as g
+    grid = torch.zeros(100, dtype=torch.float64)
+    f = torch.zeros(2 * 5 * 3, dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        g.gram_noalloc(4, [5, 5], [10, 10], grid, [f])            # d not 2 or 3
+    with pytest.raises(ValueError):
+        g.gram_noalloc(2, [5, 5], [10, 10], grid, [])             # no field
+    with pytest.raises(ValueError):
+        g.gram_noalloc(2, [5, 5], [10, 10], grid, [f, f, f])      # more fields than d
+    with pytest.raises(ValueError):
+        g.gram_noalloc(2, [5, 5], [10, 10], grid, [f])            # host tensors
