@@ -209,3 +209,24 @@ def test_sphere_bounds_3d_small():
     assert U[0, 0] > lo and L[0, 0] < hi
     assert np.abs(U - U[0, 0] * np.eye(3)).max() < 1e-9 * U[0, 0]    # cubic symmetry
     assert mat.harmonic_mean() < L[0, 0] and U[0, 0] < mat.mean()
+
+
+@pytest.mark.parametrize("d,kind", [(2, "primal"), (2, "dual"), (3, "primal"), (3, "dual")])
+def test_admissible_projection(d, kind):
+    """The nearest admissible fluctuation (Def. trig_pol, Def. projection):
+    identity on admissible fields, idempotent, Hermitian and in the range of G;
+    on a perturbed admissible field it removes exactly the perturbation's
+    non-Hermitian and out-of-range parts."""
+    rng = np.random.default_rng(17 + d)
+    N = [7, 9] if d == 2 else [5, 7, 3]
+    x = W.random_field(rng, d, N, hermitian=False)
+    a = G.admissible(x, kind)
+    flip = a[(slice(None),) + (slice(None, None, -1),) * d]
+    assert np.abs(a - np.conj(flip)).max() < 1e-14 * np.abs(a).max()          # Hermitian
+    assert np.abs(G.project(a, kind) - a).max() < 1e-14 * np.abs(a).max()      # in range(G)
+    assert np.abs(G.admissible(a, kind) - a).max() < 1e-14 * np.abs(a).max()  # idempotent
+    h = G.project(W.random_field(rng, d, N), kind)                              # admissible
+    assert np.abs(G.admissible(h, kind) - h).max() < 1e-14 * np.abs(h).max()
+    # the removed part is orthogonal to every admissible field
+    r = x - a
+    assert abs(G.inner(r, h)) < 1e-12 * np.sqrt(G.inner(r, r) * G.inner(h, h))
