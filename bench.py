@@ -503,26 +503,30 @@ def run_ours(args, world, rank, local):
                    "sample": f"failed: {ex}"}
 
     if rank == 0:
-        summary = {"mixed_pairs_per_s": value / world,
-                   "mixed_grid_pt_iter_per_s": gpi / world}
+        def r3(x):
+            return None if x is None else float(f"{x:.3g}")
+
+        # compact summary, printed last: a reader of the line's tail sees it
+        summary = {"mixed": {"pairs_per_s": r3(value / world), "gpt_iter_per_s": r3(gpi / world)}}
         if fp64:
-            summary.update({"fp64_pairs_per_s": fp64["bound_pairs_per_s"],
-                            "fp64_grid_pt_iter_per_s": fp64["grid_pt_iter_per_s"],
-                            "mixed_speedup": fp64["mixed_speedup"],
-                            "rel_err_mixed_vs_fp64": max(fp64["rel_err_upper"], fp64["rel_err_lower"])})
+            summary["fp64"] = {"pairs_per_s": r3(fp64["bound_pairs_per_s"]),
+                               "gpt_iter_per_s": r3(fp64["grid_pt_iter_per_s"])}
+            summary["mixed_speedup"] = r3(fp64["mixed_speedup"])
+            summary["rel_err_mixed_vs_fp64"] = r3(max(fp64["rel_err_upper"], fp64["rel_err_lower"]))
         if d3:
-            summary["d3"] = {f'{c["shape"]}{c["N"]}': {k: c.get(k) for k in ("mixed_pairs_per_s", "fp64_pairs_per_s",
-                                                                              "mixed_speedup", "rel_err_upper")}
-                             for c in d3["cases"]}
+            summary["d3[mixed,fp64,speedup,rel_err]"] = {
+                f'{c["shape"]}{c["N"]}': [r3(c.get(k)) for k in ("mixed_pairs_per_s", "fp64_pairs_per_s",
+                                                                 "mixed_speedup", "rel_err_upper")]
+                for c in d3["cases"]}
         if batched:
-            summary["batched"] = {"pairs_per_s": batched["bound_pairs_per_s"],
-                                  "sample_speedup_vs_fp64_single": batched["sample"]["speedup_vs_fp64_single"]}
+            summary["batched[pairs_s,x_fp64_single]"] = [r3(batched["bound_pairs_per_s"]),
+                                                         r3(batched["sample"]["speedup_vs_fp64_single"])]
         if served:
-            summary["served"] = {arm: {"rate": served[arm]["rate_req_per_s"],
-                                       "pairs_per_s": served[arm]["bound_pairs_per_s"],
-                                       "p50_ms": served[arm]["latency_ms"]["p50"],
-                                       "p99_ms": served[arm]["latency_ms"]["p99"]}
-                                 for arm in ("mixed", "fp64", "overload") if arm in served}
+            summary["served[rate,pairs_s,p50_ms,p99_ms]"] = {
+                arm: [r3(served[arm]["rate_req_per_s"]), r3(served[arm]["bound_pairs_per_s"]),
+                      r3(served[arm]["latency_ms"]["p50"]), r3(served[arm]["latency_ms"]["p99"])]
+                for arm in ("mixed", "fp64", "overload") if arm in served}
+        summary["roofline_frac"] = r3(roof["frac"])
         top = dict(list(kernels.items())[:8])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -533,15 +537,8 @@ def run_ours(args, world, rank, local):
                        "precision": "mixed: FP32 inner CG, FP64 residual correction, FP64 projection and Gram",
                        "tol": 1e-10, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (per-step working set ~1.5 GB)"},
-            "summary": summary,
-            "roofline": roof,
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
-            "e2e": {"value": pairs / e2e_t / args.steps * args.steps if e2e_ts else None, "unit": UNIT,
-                    "h2d_bytes_per_step": phase_bytes, "d2h_bytes_per_step": out_bytes,
-                    "what": "ghb_create (device set-up from the host inclusion list) + ghb_bounds "
-                            "(results to host) + ghb_destroy, host wall clock"},
-            "cpu_baseline": cpu,
+            "kernels_top": top,
+            "bounds": {"upper": U.tolist(), "lower": L.tolist()},
             "grid_pt_iter_per_s": gpi,
             "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                             int(0.99 * len(lat_ms)))]},
@@ -553,8 +550,15 @@ def run_ours(args, world, rank, local):
             "warm_start": warm,
             "reduced": reduced,
             "image": image,
-            "bounds": {"upper": U.tolist(), "lower": L.tolist()},
-            "kernels_top": top,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": {"value": pairs / e2e_t / args.steps * args.steps if e2e_ts else None, "unit": UNIT,
+                    "h2d_bytes_per_step": phase_bytes, "d2h_bytes_per_step": out_bytes,
+                    "what": "ghb_create (device set-up from the host inclusion list) + ghb_bounds "
+                            "(results to host) + ghb_destroy, host wall clock"},
+            "cpu_baseline": cpu,
+            "roofline": roof,
+            "summary": summary,
         }
         if line["e2e"]["value"] is not None:
             line["e2e"]["value"] = world / e2e_t
