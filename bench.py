@@ -77,11 +77,13 @@ def parse():
     ap.add_argument("--serve-overload-rate", type=float, default=200.0,
                     help="arrival rate of the short overload run (0 = skip)")
     ap.add_argument("--serve-overload-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-overload-drain", type=float, default=10.0,
+                    help="seconds after the overload run's last arrival before it stops waiting")
     ap.add_argument("--serve-drain", type=float, default=30.0,
                     help="seconds after the last arrival before a served run stops waiting")
     ap.add_argument("--serve-slots", type=int, default=64,
                     help="requests the server solves at once (more wait in its queue)")
-    ap.add_argument("--serve-fp64-seconds", type=float, default=20.0,
+    ap.add_argument("--serve-fp64-seconds", type=float, default=10.0,
                     help="measured arrival window of the plain FP64 served run (0 = skip)")
     ap.add_argument("--matvec-workload", choices=["disk", "sphere"], default="disk",
                     help="--matvec-only: the d = 2 disk (default) or the d = 3 sphere of volume fraction 0.2, "
@@ -271,6 +273,8 @@ def run_reference(args, world, rank):
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
+
+    t_bench0 = time.perf_counter()
 
     import paper_1412_2033_gb300 as g
 
@@ -557,6 +561,7 @@ def run_ours(args, world, rank, local):
                     "what": "ghb_create (device set-up from the host inclusion list) + ghb_bounds "
                             "(results to host) + ghb_destroy, host wall clock"},
             "cpu_baseline": cpu,
+            "bench_wall_s": round(time.perf_counter() - t_bench0, 1),
             "roofline": roof,
             "summary": summary,
         }
@@ -770,9 +775,9 @@ def run_served(args, g):
                            "window_s": args.serve_overload_seconds,
                            "note": "beyond one GPU's capacity: latencies are queueing times",
                            **_serve_mixed(g, so, args.serve_slots, 0.0, args.serve_overload_seconds,
-                                          args.serve_drain)}
+                                          args.serve_overload_drain)}
     if args.serve_fp64_seconds > 0:
-        probe64 = probe[: max(4, args.serve_probe // 4)]
+        probe64 = probe[: max(6, args.serve_probe // 8)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for m in probe64:
