@@ -25,13 +25,15 @@ def ghb():
 
 
 SQUARE = dict(d=2, N=[15, 15], a0=1.0, inclusions=[(0, (0, 0, 0), (2 ** -0.5, 2 ** -0.5, 1), 10.0)])
+BALL_BOX = dict(d=3, N=[9, 7, 11], a0=2.0, inclusions=[
+    (2, (0.1, -0.2, 0.05), (0.3, 0, 0), 50.0), (0, (-0.3, 0.3, -0.3), (0.2, 0.3, 0.25), 0.1)])
 
 
 @pytest.mark.parametrize("kind", ["primal", "dual"])
-def test_history_fp64_matches_oracle(ghb, kind):
-    m = SQUARE
+@pytest.mark.parametrize("m", [SQUARE, BALL_BOX], ids=["square_N15", "d3_ball_box"])
+def test_history_fp64_matches_oracle(ghb, kind, m):
     mat = OC.material_from_dict(m)
-    E = [1.0, 0.4]
+    E = [1.0, 0.4, -0.7][:m["d"]]
     op = OG.Operator(mat, m["N"], kind)
     _, info = OG.cg(op, op.rhs(E), 1e-10, track_energy_E=E)
     ref = np.array(info["energies"])
@@ -47,10 +49,10 @@ def test_history_fp64_matches_oracle(ghb, kind):
     assert abs(en[0] - voigt) < 1e-13 * voigt                        # the Voigt (Reuss) start
 
 
-def test_prolong_is_a_copy(ghb):
-    rng = np.random.default_rng(4)
-    Nc, Nf = [9, 7], [21, 15]
-    xc = W.random_field(rng, 2, Nc)
+@pytest.mark.parametrize("Nc,Nf", [([9, 7], [21, 15]), ([5, 7, 3], [9, 11, 7]), ([3, 3, 3], [3, 5, 9])])
+def test_prolong_is_a_copy(ghb, Nc, Nf):
+    rng = np.random.default_rng(4 + len(Nc))
+    xc = W.random_field(rng, len(Nc), Nc)
     ref = ghb.half_from_full(OG.prolong(xc, Nf))
     xt = torch.from_numpy(np.ascontiguousarray(ghb.half_from_full(xc))).cuda()
     got = ghb.prolong(xt, Nf).cpu().numpy()
@@ -58,17 +60,18 @@ def test_prolong_is_a_copy(ghb):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_warm_start(ghb, precision):
-    N, Nc = 81, 27
-    m = W.centred_disk(N, fraction=0.3, value=100.0)
-    mc = dict(m, N=[Nc, Nc])
-    E = [1.0, 0.0]
+@pytest.mark.parametrize("d,N,Nc", [(2, 81, 27), (3, 27, 9)])
+def test_warm_start(ghb, precision, d, N, Nc):
+    m = W.centred_disk(N, fraction=0.3, value=100.0) if d == 2 else W.centred_sphere(N, fraction=0.2, value=1000.0)
+    mc = dict(m, N=[Nc] * d)
+    E = [1.0] + [0.0] * (d - 1)
     cc = ghb.Context.from_microstructure(mc, precision=precision)
     fc, ic, _, _ = cc.solve_ex(E)
     ec = fc.clone()
-    ec[0, (Nc - 1) // 2, 0] -= E[0]                  # the fluctuation of the coarse field
-    ec[1, (Nc - 1) // 2, 0] -= E[1]
-    x0 = ghb.prolong(ec, [N, N])
+    zero = (Nc - 1) // 2
+    for i in range(d):                               # the fluctuation of the coarse field
+        ec[(i,) + (zero,) * (d - 1) + (0,)] -= E[i]
+    x0 = ghb.prolong(ec, [N] * d)
     cf = ghb.Context.from_microstructure(m, precision=precision)
     fw, iw, ew, sw = cf.solve_ex(E, x0=x0, energies=True)
     fz, iz, ez, sz = cf.solve_ex(E, energies=True)
