@@ -102,7 +102,9 @@ typedef struct {
   int32_t max_iter;    /* per solve, counted in operator applications (default 20000) */
   int32_t precision;   /* GHB_FP64 (default) or GHB_MIXED */
   double inner_tol;    /* GHB_MIXED: relative reduction asked of each FP32 inner
-                          solve (default 1e-5) */
+                          solve (default 1e-5); a solve that needs less to
+                          reach tol is asked half of what it needs (at most
+                          1/2) */
   int32_t max_outer;   /* GHB_MIXED: cap on FP64 residual corrections (default 20) */
   int32_t M[3];        /* double grid per axis; 0 = automatic: the smallest
                           M_a >= 2 N_a - 1 whose prime factors are 2, 3, 5.

@@ -788,8 +788,8 @@ ghb_status solve(ghb_ctx* c, int kind, const double* E, double2* field_out, ghb_
                                    cudaMemcpyDeviceToDevice, c->stream));
       int it = 0, dn = 0;
       double rr32 = 0, bb32 = 0;
-      TRY(cg_run<float2>(c, kind, c->w32.q, c->opt.inner_tol, maxiter - total_inner, &it, &dn, &rr32,
-                         &bb32));
+      const double itol = inner_target(c->opt.inner_tol, tol, rr, bb);
+      TRY(cg_run<float2>(c, kind, c->w32.q, itol, maxiter - total_inner, &it, &dn, &rr32, &bb32));
       total_inner += it;
       mv32 += it;
       if (dn == BREAKDOWN && it == 0) {

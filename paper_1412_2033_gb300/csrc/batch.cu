@@ -659,7 +659,7 @@ ghb_status start_inner(ghb_batch* b, const std::vector<Slot*>& ss) {
     i.b = s->b32;
     i.st = &b->d_states[s->sidx];
     i.partials = s->partials;
-    i.tol = b->opt.inner_tol;
+    i.tol = inner_target(b->opt.inner_tol, b->opt.tol, b->h_states[s->sidx].rr, s->bb);
     i.maxiter = std::max(1, b->opt.max_iter - s->inner_iters);
     init.push_back(i);
   }

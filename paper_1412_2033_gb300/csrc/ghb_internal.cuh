@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -61,6 +63,17 @@ struct CgState {
 };
 
 constexpr int kMaxPartials = 4096;
+
+// Relative reduction asked of an FP32 inner solve that starts from the FP64
+// residual <r, r> = rr of a solve with <b, b> = bb and outer tolerance tol:
+// inner_tol, or half of what the outer tolerance still needs when that is
+// less (so a last correction that only has to gain a small factor takes a
+// few FP32 iterations instead of a full inner_tol reduction), at most 1/2.
+inline double inner_target(double inner_tol, double tol, double rr, double bb) {
+  if (!(rr > 0.0) || !(bb > 0.0)) return inner_tol;
+  const double need = 0.5 * tol * std::sqrt(bb / rr);
+  return std::min(0.5, std::max(inner_tol, need));
+}
 
 // ---------------------------------------------------------------------------
 // inclusions on the device
