@@ -86,14 +86,20 @@ __host__ __device__ constexpr int ct_min_units() {
 }
 // Threads of a column-pass CTA.  Runtime plans: 512 (FP32) or 256 (FP64).
 // Size-specialised transforms: one thread per butterfly of the pass with the
-// fewest (TW lines of ct_min_units each), in whole warps, between 128 and 512
-// (FP32) or 256 (FP64) -- FP64 holds a radix group of up to 27 complex
+// fewest (TW lines of ct_min_units each), in whole warps, between 128 and 672
+// (FP32) or 352 (FP64) -- FP64 holds a radix group of up to 27 complex
 // doubles per thread, which needs more than the 128 registers a 512-thread
-// CTA allows.  col_min_blocks keeps the register budget of a full block.
-template <typename T, int TW, int MCT>
+// CTA allows.  At M = 4374 the 4 x 162 FP32 (2 x 162 FP64) radix-27
+// butterflies of a tile take one round of 672 (352) threads instead of two
+// rounds of 512 (256), the second about a quarter full: FP32 axis-1 inverse
+// 68 -> 60 us, forward 64 -> 61 us; FP64 1.20 -> 1.15 ms each.  672 threads
+// leave 80 registers, which the FP32 inverse pass with the p update exceeds
+// (it spilled and measured 89 against 86 us), so the p-update variants keep
+// 512 (256).  col_min_blocks keeps the register budget of a full block.
+template <typename T, int TW, int MCT, int MODE = COL_PLAIN>
 __host__ __device__ constexpr int col_threads() {
   if constexpr (MCT != 0) {
-    constexpr int full = sizeof(T) == 4 ? 512 : 256;
+    constexpr int full = sizeof(T) == 4 ? (MODE == COL_PUPDATE ? 512 : 672) : (MODE == COL_PUPDATE ? 256 : 352);
     int t = ((ct_min_units<MCT>() * TW + 31) / 32) * 32;
     if (t < 128) t = 128;
     return t < full ? t : full;
@@ -101,10 +107,10 @@ __host__ __device__ constexpr int col_threads() {
     return sizeof(T) == 8 ? 256 : 512;
   }
 }
-template <typename T, int TW, int MCT>
+template <typename T, int TW, int MCT, int MODE = COL_PLAIN>
 __host__ __device__ constexpr int col_min_blocks() {
   constexpr int full = sizeof(T) == 4 ? 512 : 256;
-  return (full + col_threads<T, TW, MCT>() - 1) / col_threads<T, TW, MCT>();
+  return (full + col_threads<T, TW, MCT, MODE>() - 1) / col_threads<T, TW, MCT, MODE>();
 }
 
 // ---------------------------------------------------------------------------
@@ -205,7 +211,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
       pnew = static_cast<C*>(a.pnew);
     }
     ColSource<C, T, MODE == COL_PUPDATE> src{in, pold, pnew, s_in, beta, static_cast<int>(a.inner), half, M, width};
-    fft_dit_ct_src<+1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, src);
+    fft_dit_ct_src<+1, TW, col_threads<T, TW, MCT, MODE>(), MCT>(buf, tw, src);
     C* __restrict__ out = static_cast<C*>(a.out);
     for (int u = threadIdx.x; u < M * TW; u += blockDim.x) {
       const int t = u % TW;
@@ -233,7 +239,7 @@ __device__ __forceinline__ void col_body(const ColArgs& a, const FftPlan& pl, in
       const int i = n <= half ? n + half : (n >= M - half ? n - M + half : -1);
       if (i >= 0 && t < width) out[s_out[t] + i * static_cast<int>(a.inner)] = inv * v;
     };
-    fft_dif_ct_snk<-1, TW, col_threads<T, TW, MCT>(), MCT>(buf, tw, snk);
+    fft_dif_ct_snk<-1, TW, col_threads<T, TW, MCT, MODE>(), MCT>(buf, tw, snk);
   } else if (SIGN > 0) {
     const C* __restrict__ in = static_cast<const C*>(a.in);
     const int Lin = a.Lin;
@@ -335,7 +341,7 @@ constexpr int kColThreads32 = 512;
 constexpr int kColThreads64 = 256;
 
 template <typename T, int TW, int SIGN, int MODE, int MCT = 0>
-__global__ void __launch_bounds__(col_threads<T, TW, MCT>(), col_min_blocks<T, TW, MCT>())
+__global__ void __launch_bounds__(col_threads<T, TW, MCT, MODE>(), col_min_blocks<T, TW, MCT, MODE>())
     col_kernel(ColArgs a, FftPlan pl) {
   col_body<T, TW, SIGN, MODE, MCT>(a, pl, blockIdx.x);
 }
@@ -376,7 +382,7 @@ inline ghb_status launch_col_t(const ColArgs& a, const FftPlan& pl, cudaStream_t
     set_error("column pass operand of 2^31 entries or more");
     return GHB_ERR_INVALID;
   }
-  const int threads = MCT != 0 ? col_threads<T, TW, MCT>()
+  const int threads = MCT != 0 ? col_threads<T, TW, MCT, MODE>()
                                : ((sizeof(T) == 4 && pl.M * TW >= 2048) ? kColThreads32 : 256);
   col_kernel<T, TW, SIGN, MODE, MCT><<<static_cast<unsigned>(grid), threads, smem, s>>>(a, pl);
   GHB_CUDA_TRY(cudaGetLastError());
