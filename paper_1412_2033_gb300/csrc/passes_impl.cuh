@@ -107,10 +107,19 @@ __host__ __device__ constexpr int col_threads() {
     return sizeof(T) == 8 ? 256 : 512;
   }
 }
+// Resident blocks the compiler must allow for: as many as make up a full
+// block's threads; FP32 one fewer when that leaves fewer than the 96
+// registers a radix-27 group needs (448 threads at M = 1458 were held to 72
+// registers by two blocks and spilled 208 bytes: p-update inverse pass
+// 19.4 -> 17.0 us).  (FP64 at M = 1458 measured 3 % slower with one block.)
 template <typename T, int TW, int MCT, int MODE = COL_PLAIN>
 __host__ __device__ constexpr int col_min_blocks() {
   constexpr int full = sizeof(T) == 4 ? 512 : 256;
-  return (full + col_threads<T, TW, MCT, MODE>() - 1) / col_threads<T, TW, MCT, MODE>();
+  constexpr int t = col_threads<T, TW, MCT, MODE>();
+  constexpr int need = sizeof(T) == 4 ? 96 : 0;
+  int b = (full + t - 1) / t;
+  if (b > 1 && 65536 / (b * t) < need) --b;
+  return b;
 }
 
 // ---------------------------------------------------------------------------
@@ -435,6 +444,15 @@ struct LineDesc {
   int valid;
 };
 
+
+// Field f of a row pass.  Selects rather than an index into the argument's
+// array: a run-time index into a kernel parameter makes the compiler copy the
+// whole argument to local memory and load the pointer from there (the FP32
+// last-axis pass at M = 4374: 164 -> 145 us without that copy and without
+// the per-entry line masks of its staged spectra).
+__device__ __forceinline__ void* row_field(const RowArgs& a, int f) {
+  return f == 0 ? a.t[0] : (f == 1 ? a.t[1] : a.t[2]);
+}
 template <typename T, int NL, int MODE>
 __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, int rows_per_cta,
                                          int64_t bid, int64_t nb) {
@@ -479,9 +497,9 @@ __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, in
       const LineDesc d0 = ld[2 * j], d1 = ld[2 * j + 1];
       C A = mk(T(0), T(0)), B = mk(T(0), T(0));
       if (d0.valid)
-        A = static_cast<const C*>(a.t[d0.field])[d0.comp * a.comp_stride + d0.row * H + k];
+        A = static_cast<const C*>(row_field(a, d0.field))[d0.comp * a.comp_stride + d0.row * H + k];
       if (d1.valid)
-        B = static_cast<const C*>(a.t[d1.field])[d1.comp * a.comp_stride + d1.row * H + k];
+        B = static_cast<const C*>(row_field(a, d1.field))[d1.comp * a.comp_stride + d1.row * H + k];
       buf[pidx<C>(__ldg(&perm[k]) * NL + j)] = mk(A.x - B.y, A.y + B.x);
       if (k > 0) buf[pidx<C>(__ldg(&perm[M - k]) * NL + j)] = mk(A.x + B.y, B.x - A.y);
     }
@@ -509,10 +527,10 @@ __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, in
         const C W = buf[pidx<C>(__ldg(&perm[k]) * NL + j)];
         const C Wm = buf[pidx<C>(__ldg(&perm[k == 0 ? 0 : M - k]) * NL + j)];
         if (d0.valid)
-          static_cast<C*>(a.t[d0.field])[d0.comp * a.comp_stride + d0.row * H + k] =
+          static_cast<C*>(row_field(a, d0.field))[d0.comp * a.comp_stride + d0.row * H + k] =
               mk(sc * (W.x + Wm.x), sc * (W.y - Wm.y));
         if (d1.valid)
-          static_cast<C*>(a.t[d1.field])[d1.comp * a.comp_stride + d1.row * H + k] =
+          static_cast<C*>(row_field(a, d1.field))[d1.comp * a.comp_stride + d1.row * H + k] =
               mk(sc * (W.y + Wm.y), sc * (Wm.x - W.x));
       }
     } else if (MODE == ROW_TOREAL) {
@@ -673,17 +691,22 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     return d;
   };
   // Copies of the half spectra of the lines described by L[0 .. 2NL) into the
-  // staging area.  Long rows (H >= the block): line by line, the block
-  // striding over k.  Short rows: one flat loop over (line, k), the line and k
-  // of a thread advanced by the block size each step (no division per entry).
+  // staging area; a line that is not valid (past the last row) gets zeros,
+  // so that the transforms read the staged pairs without masks.  Long rows
+  // (H >= the block): line by line, the block striding over k.  Short rows:
+  // one flat loop over (line, k), the line and k of a thread advanced by the
+  // block size each step (no division per entry).
   auto issue_from = [&](const LineDesc* L) {
     if (H >= static_cast<int>(blockDim.x)) {
 #pragma unroll 1
       for (int rho = 0; rho < 2 * NL; ++rho) {
         const LineDesc d = L[rho];
-        if (!d.valid) continue;
-        const C* src = static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H;
         C* dst = sin + (rho >> 1) * 2 * SH + (rho & 1);
+        if (!d.valid) {
+          for (int k = threadIdx.x; k < H; k += blockDim.x) dst[2 * k] = mk(T(0), T(0));
+          continue;
+        }
+        const C* src = static_cast<const C*>(row_field(a, d.field)) + d.comp * a.comp_stride + d.row * H;
         for (int k = threadIdx.x; k < H; k += blockDim.x) cp_async<sizeof(C)>(dst + 2 * k, src + k);
       }
       return;
@@ -693,9 +716,11 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     int k = static_cast<int>(threadIdx.x) - rho * H;
     while (rho < 2 * NL) {
       const LineDesc d = L[rho];
+      C* dst = sin + ((rho >> 1) * SH + k) * 2 + (rho & 1);
       if (d.valid)
-        cp_async<sizeof(C)>(sin + ((rho >> 1) * SH + k) * 2 + (rho & 1),
-                            static_cast<const C*>(a.t[d.field]) + d.comp * a.comp_stride + d.row * H + k);
+        cp_async<sizeof(C)>(dst, static_cast<const C*>(row_field(a, d.field)) + d.comp * a.comp_stride + d.row * H + k);
+      else
+        *dst = mk(T(0), T(0));
       rho += step_r;
       k += step_k;
       if (k >= H) {
@@ -751,25 +776,24 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
         const bool lo = n < H, hi = n > M - H;
         const int k = lo ? n : M - n;
         C A = mk(T(0), T(0)), B = mk(T(0), T(0));
-        if (lo || hi) {
-          // both real lines in one load; a line that is not valid this group
-          // holds stale entries, which the mask drops
+        if (lo || hi) {   // both real lines in one load (zeros for a line that is not valid)
           const Pair v = spair[j * SH + k];
-          const int msk = lmask[j];
-          if (msk & 1) A = v.a;
-          if (msk & 2) B = v.b;
+          A = v.a;
+          B = v.b;
         }
         return lo ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
       };
       // multiply by A_M between the transforms, in registers
       auto mul = [&](int j, int m, C z) -> C {
         T a0 = T(0), a1 = T(0);
-        const int msk = lmask[j];
         const int2 ro = lrow[j];
         if constexpr (row_streams_multiplier<T, MCT>()) {
-          if (msk & 1) a0 = __ldg(&am[ro.x + m]);
-          if (msk & 2) a1 = __ldg(&am[ro.y + m]);
+          // a line that is not valid reads row 0 (in bounds, finite) and is
+          // not stored; its zero input keeps the other line of the pair exact
+          a0 = __ldg(&am[ro.x + m]);
+          a1 = __ldg(&am[ro.y + m]);
         } else {
+          const int msk = lmask[j];
           if (msk & 1) a0 = sa[ro.x + m];
           if (msk & 2) a1 = sa[ro.y + m];
         }
@@ -835,10 +859,10 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
       const C W = buf[bix<MCT, C>(__ldg(&perm[k]) * NL + j)];
       const C Wm = buf[bix<MCT, C>(__ldg(&perm[k == 0 ? 0 : M - k]) * NL + j)];
       if (d0.valid)
-        static_cast<C*>(a.t[d0.field])[d0.comp * a.comp_stride + d0.row * H + k] =
+        static_cast<C*>(row_field(a, d0.field))[d0.comp * a.comp_stride + d0.row * H + k] =
             mk(sc * (W.x + Wm.x), sc * (W.y - Wm.y));
       if (d1.valid)
-        static_cast<C*>(a.t[d1.field])[d1.comp * a.comp_stride + d1.row * H + k] =
+        static_cast<C*>(row_field(a, d1.field))[d1.comp * a.comp_stride + d1.row * H + k] =
             mk(sc * (W.y + Wm.y), sc * (Wm.x - W.x));
     }
     __syncthreads();
