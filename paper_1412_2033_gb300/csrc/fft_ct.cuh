@@ -118,10 +118,43 @@ __device__ __forceinline__ void substage_const(C* v) {
   if constexpr (JP + 1 < SIG) substage_const<SIGN, DIT, RHO, SIG, RG, JP + 1>(v);
 }
 
-template <int SIGN, bool DIT, bool FIRST, int RHO, int SIG, int RG, int TS, typename C>
+// One sub-stage with every twiddle read from the length-M table: entry offset
+// JP < SIG of the sub-stage takes (w_{L_s}^p w_{SIG RHO}^JP)^q = w_M^(q B),
+// B = TS p + JP M / (SIG RHO), for q = 1 .. RHO-1 (q B < M).  FP64 passes are
+// bound by the FP64 pipe, so table loads replace the complex products that
+// substage_jp spends on forming the powers (a fifth of their twiddle work).
+template <int SIGN, bool DIT, int RHO, int SIG, int RG, int JP, int TS, int M, typename C>
+__device__ __forceinline__ void substage_tab(C* v, int p, const C* __restrict__ tw) {
+  const int b = TS * p + JP * (M / (SIG * RHO));
+  C tq[RHO];
+#pragma unroll
+  for (int q = 1; q < RHO; ++q) tq[q] = __ldg(&tw[q * b]);
+#pragma unroll
+  for (int jb = 0; jb < RG / (SIG * RHO); ++jb) {
+    C e[RHO];
+#pragma unroll
+    for (int q = 0; q < RHO; ++q) e[q] = v[jb * SIG * RHO + JP + q * SIG];
+    if constexpr (DIT) {
+#pragma unroll
+      for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
+    }
+    dft_small<SIGN, RHO>(e);
+    if constexpr (!DIT) {
+#pragma unroll
+      for (int q = 1; q < RHO; ++q) e[q] = twmul<SIGN>(e[q], tq[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RHO; ++q) v[jb * SIG * RHO + JP + q * SIG] = e[q];
+  }
+  if constexpr (JP + 1 < SIG) substage_tab<SIGN, DIT, RHO, SIG, RG, JP + 1, TS, M>(v, p, tw);
+}
+
+template <int SIGN, bool DIT, bool FIRST, int RHO, int SIG, int RG, int TS, int M, typename C>
 __device__ __forceinline__ void ct_substage(C* v, int p, const C* __restrict__ tw) {
   if constexpr (FIRST) {
     substage_const<SIGN, DIT, RHO, SIG, RG, 0>(v);
+  } else if constexpr (sizeof(C) == 16) {
+    substage_tab<SIGN, DIT, RHO, SIG, RG, 0, TS, M>(v, p, tw);
   } else {
     const C wb = __ldg(&tw[p * TS]);   // w_{L_s}^p
     substage_jp<SIGN, DIT, RHO, SIG, RG, 0>(v, wb);
@@ -212,13 +245,13 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw, const 
       for (int j = 0; j < RG; ++j) src.write_back(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j), v[j]);
     }
     if constexpr (DIT) {
-      ct_substage<SIGN, DIT, FIRST, RA, 1, RG, tsA>(v, p, tw);
-      if constexpr (RB > 1) ct_substage<SIGN, DIT, FIRST, RB, RA, RG, tsB>(v, p, tw);
-      if constexpr (RC > 1) ct_substage<SIGN, DIT, FIRST, RC, RA * RB, RG, tsC>(v, p, tw);
+      ct_substage<SIGN, DIT, FIRST, RA, 1, RG, tsA, M>(v, p, tw);
+      if constexpr (RB > 1) ct_substage<SIGN, DIT, FIRST, RB, RA, RG, tsB, M>(v, p, tw);
+      if constexpr (RC > 1) ct_substage<SIGN, DIT, FIRST, RC, RA * RB, RG, tsC, M>(v, p, tw);
     } else {
-      if constexpr (RC > 1) ct_substage<SIGN, DIT, FIRST, RC, RA * RB, RG, tsC>(v, p, tw);
-      if constexpr (RB > 1) ct_substage<SIGN, DIT, FIRST, RB, RA, RG, tsB>(v, p, tw);
-      ct_substage<SIGN, DIT, FIRST, RA, 1, RG, tsA>(v, p, tw);
+      if constexpr (RC > 1) ct_substage<SIGN, DIT, FIRST, RC, RA * RB, RG, tsC, M>(v, p, tw);
+      if constexpr (RB > 1) ct_substage<SIGN, DIT, FIRST, RB, RA, RG, tsB, M>(v, p, tw);
+      ct_substage<SIGN, DIT, FIRST, RA, 1, RG, tsA, M>(v, p, tw);
     }
 #pragma unroll
     for (int j = 0; j < RG; ++j) {
@@ -314,14 +347,14 @@ __device__ __forceinline__ void ct_inverse_scale_forward(C* buf, const C* __rest
     C v[RG];
 #pragma unroll
     for (int j = 0; j < RG; ++j) v[j] = base[j * step];
-    ct_substage<SIGN_I, true, false, RA, 1, RG, tsA>(v, p, tw);
-    if constexpr (RB > 1) ct_substage<SIGN_I, true, false, RB, RA, RG, tsB>(v, p, tw);
-    if constexpr (RC > 1) ct_substage<SIGN_I, true, false, RC, RA * RB, RG, tsC>(v, p, tw);
+    ct_substage<SIGN_I, true, false, RA, 1, RG, tsA, M>(v, p, tw);
+    if constexpr (RB > 1) ct_substage<SIGN_I, true, false, RB, RA, RG, tsB, M>(v, p, tw);
+    if constexpr (RC > 1) ct_substage<SIGN_I, true, false, RC, RA * RB, RG, tsC, M>(v, p, tw);
 #pragma unroll
     for (int j = 0; j < RG; ++j) v[j] = mul(line, p + j * LP, v[j]);
-    if constexpr (RC > 1) ct_substage<SIGN_F, false, false, RC, RA * RB, RG, tsC>(v, p, tw);
-    if constexpr (RB > 1) ct_substage<SIGN_F, false, false, RB, RA, RG, tsB>(v, p, tw);
-    ct_substage<SIGN_F, false, false, RA, 1, RG, tsA>(v, p, tw);
+    if constexpr (RC > 1) ct_substage<SIGN_F, false, false, RC, RA * RB, RG, tsC, M>(v, p, tw);
+    if constexpr (RB > 1) ct_substage<SIGN_F, false, false, RB, RA, RG, tsB, M>(v, p, tw);
+    ct_substage<SIGN_F, false, false, RA, 1, RG, tsA, M>(v, p, tw);
 #pragma unroll
     for (int j = 0; j < RG; ++j) base[j * step] = v[j];
   }
