@@ -83,7 +83,7 @@ def parse():
                     help="seconds after the last arrival before a served run stops waiting")
     ap.add_argument("--serve-slots", type=int, default=64,
                     help="requests the server solves at once (more wait in its queue)")
-    ap.add_argument("--serve-fp64-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-fp64-seconds", type=float, default=30.0,
                     help="measured arrival window of the plain FP64 served run (0 = skip)")
     ap.add_argument("--matvec-workload", choices=["disk", "sphere"], default="disk",
                     help="--matvec-only: the d = 2 disk (default) or the d = 3 sphere of volume fraction 0.2, "
