@@ -444,7 +444,6 @@ struct LineDesc {
   int valid;
 };
 
-
 // Field f of a row pass.  Selects rather than an index into the argument's
 // array: a run-time index into a kernel parameter makes the compiler copy the
 // whole argument to local memory and load the pointer from there (the FP32
@@ -453,6 +452,7 @@ struct LineDesc {
 __device__ __forceinline__ void* row_field(const RowArgs& a, int f) {
   return f == 0 ? a.t[0] : (f == 1 ? a.t[1] : a.t[2]);
 }
+
 template <typename T, int NL, int MODE>
 __device__ __forceinline__ void row_body(const RowArgs& a, const FftPlan& pl, int rows_per_cta,
                                          int64_t bid, int64_t nb) {
