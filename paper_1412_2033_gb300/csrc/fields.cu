@@ -6,6 +6,8 @@
 // (u, v) = sum_{k in Z_N} u(k).conj v(k)) is evaluated on the half spectrum as
 // sum_k w_k Re(u(k).conj v(k)) with weight w_k = 1 on the plane k_d = 0 and 2
 // elsewhere (each stored k_d > 0 stands for k and -k).
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "ghb_internal.cuh"
@@ -757,9 +759,33 @@ ghb_status launch_gram_zn(const GramZnArgs& ga, const double2* tab, const Geomet
 }
 
 namespace {
+// Blocks of one vector-operation launch: the field's grid, but at most the
+// blocks of this kernel that are resident on the device at once (the loops
+// stride over the field, so one full wave does the work without a partly
+// filled second wave: the FP32 projection kernel holds 5 blocks per SM, and
+// its 1216-block grid ran 1.6 waves).  The count is taken once per process
+// (one device model).
+template <typename T, int OP>
+int64_t one_wave(int64_t want) {
+  static std::atomic<int> wave{0};
+  int w = wave.load(std::memory_order_relaxed);
+  if (w == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<T, OP>, kFieldThreads, 0) != cudaSuccess ||
+        sms < 1 || per_sm < 1)
+      return want;
+    w = sms * per_sm;
+    wave.store(w, std::memory_order_relaxed);
+  }
+  return std::min<int64_t>(want, w);
+}
+
 template <typename T, int OP>
 ghb_status launch_one(const CgItem& it, cudaStream_t s) {
-  cg_kernel<T, OP><<<static_cast<unsigned>(it.nblocks), kFieldThreads, 0, s>>>(it);
+  const int64_t nb = one_wave<T, OP>(it.nblocks);
+  cg_kernel<T, OP><<<static_cast<unsigned>(nb), kFieldThreads, 0, s>>>(it);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }
