@@ -205,6 +205,16 @@ struct ct_writes_back : std::false_type {};
 template <typename S>
 struct ct_writes_back<S, std::void_t<decltype(S::kWriteBack)>> : std::integral_constant<bool, S::kWriteBack> {};
 
+// Sources with a member kRanged = true are called as src.ranged(line, nb, n0,
+// span) for input n = nb + n0, where n0 and span are compile-time constants of
+// the pass and 0 <= nb < span: a source whose entries depend on where n lies
+// (zero padding, a mirrored half) can then decide for the whole range
+// [n0, n0 + span) with a test that is the same in every thread.
+template <typename S, typename = void>
+struct ct_ranged : std::false_type {};
+template <typename S>
+struct ct_ranged<S, std::void_t<decltype(S::kRanged)>> : std::integral_constant<bool, S::kRanged> {};
+
 // One pass: butterflies of radix RA RB RC on stride LP, NT threads, NL lines
 // interleaved (element (m, line) at m NL + line, no padding).  The first pass
 // may take its entries from a source instead of the buffer (DIT: src(line, n)
@@ -238,7 +248,8 @@ __device__ __forceinline__ void ct_pass(C* buf, const C* __restrict__ tw, const 
     C v[RG];
 #pragma unroll
     for (int j = 0; j < RG; ++j) {
-      if constexpr (FROM_SRC) v[j] = src(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j));
+      if constexpr (FROM_SRC && ct_ranged<Src>::value) v[j] = src.ranged(line, nb, (M / RG) * ct_revj<RA, RB, RC>(j), M / RG);
+      else if constexpr (FROM_SRC) v[j] = src(line, nb + (M / RG) * ct_revj<RA, RB, RC>(j));
       else v[j] = base[j * step];
     }
     if constexpr (FROM_SRC && ct_writes_back<Src>::value) {

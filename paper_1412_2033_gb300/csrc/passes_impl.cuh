@@ -651,6 +651,52 @@ __host__ __device__ inline size_t row_staged_smem(int M, int H, int rows_per_cta
          static_cast<size_t>(rows_per_cta) * M * sizeof(T);
 }
 
+// Input of the size-specialised last-axis transforms: entry n of complex line
+// j is the Hermitian completion of the two staged half spectra X0, X1 of its
+// real lines (X(k), k = 0 .. H-1; line pairs at stride SH):
+//     Z(n) = X0(n) + i X1(n)                      n < H,
+//     Z(n) = conj X0(M-n) + i conj X1(M-n)        n > M - H,
+//     0                                           otherwise.
+// With RANGED, ranged() decides for a whole range of n at once (see
+// ct_ranged): in the first pass at M = 4374, N = 2187 every range but two lies
+// entirely below H, entirely above M - H or entirely in the zeros.  Measured
+// per kernel: FP64 last-axis pass 4310 -> 4256 us at M = 4374 and 4204 -> 4125
+// us at M = 270, FP32 209 -> 204 us at M = 270, but FP32 144 -> 148 us at
+// M = 4374, which therefore keeps the test per entry.
+template <typename C, typename Pair, bool RANGED>
+struct RowSource {
+  static constexpr bool kRanged = RANGED;
+  const Pair* spair;
+  int SH, H, M;
+  __device__ __forceinline__ C lo(int j, int k) const {
+    const Pair v = spair[j * SH + k];   // both real lines in one load
+    return mk(v.a.x - v.b.y, v.a.y + v.b.x);
+  }
+  __device__ __forceinline__ C hi(int j, int k) const {
+    const Pair v = spair[j * SH + k];
+    return mk(v.a.x + v.b.y, v.b.x - v.a.y);
+  }
+  __device__ __forceinline__ C operator()(int j, int n) const {
+    using T = decltype(C{}.x);
+    const bool l = n < H, h = n > M - H;
+    const int k = l ? n : M - n;
+    C A = mk(T(0), T(0)), B = mk(T(0), T(0));
+    if (l || h) {
+      const Pair v = spair[j * SH + k];
+      A = v.a;
+      B = v.b;
+    }
+    return l ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
+  }
+  __device__ __forceinline__ C ranged(int j, int nb, int n0, int span) const {
+    using T = decltype(C{}.x);
+    if (n0 + span - 1 < H) return lo(j, nb + n0);
+    if (n0 > M - H) return hi(j, M - n0 - nb);
+    if (n0 >= H && n0 + span - 1 <= M - H) return mk(T(0), T(0));
+    return (*this)(j, nb + n0);
+  }
+};
+
 template <typename T, int NL, int MCT = 0>
 __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPlan& pl, int rows_per_cta,
                                                   int64_t bid, int64_t nb) {
@@ -730,11 +776,12 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     }
   };
   auto issue_multiplier = [&](int64_t grp) {
-    if constexpr (row_streams_multiplier<T, MCT>()) return;   // read in the fused pass instead
-    for (int r = 0; r < rows_per_cta; ++r) {
-      const int64_t row = grp * rows_per_cta + r;
-      if (row >= a.rows) break;
-      for (int m = threadIdx.x; m < M; m += blockDim.x) cp_async<sizeof(T)>(sa + r * M + m, am + row * M + m);
+    if constexpr (!row_streams_multiplier<T, MCT>()) {   // else read in the fused pass instead
+      for (int r = 0; r < rows_per_cta; ++r) {
+        const int64_t row = grp * rows_per_cta + r;
+        if (row >= a.rows) break;
+        for (int m = threadIdx.x; m < M; m += blockDim.x) cp_async<sizeof(T)>(sa + r * M + m, am + row * M + m);
+      }
     }
   };
 
@@ -772,17 +819,9 @@ __device__ __forceinline__ void row_matvec_staged(const RowArgs& a, const FftPla
     // size-specialised transform reads the completed spectrum directly in its
     // first pass instead.
     if constexpr (MCT != 0) {
-      auto src = [&](int j, int n) -> C {
-        const bool lo = n < H, hi = n > M - H;
-        const int k = lo ? n : M - n;
-        C A = mk(T(0), T(0)), B = mk(T(0), T(0));
-        if (lo || hi) {   // both real lines in one load (zeros for a line that is not valid)
-          const Pair v = spair[j * SH + k];
-          A = v.a;
-          B = v.b;
-        }
-        return lo ? mk(A.x - B.y, A.y + B.x) : mk(A.x + B.y, B.x - A.y);
-      };
+      // the staged pairs hold zeros for a line that is not valid
+      constexpr bool ranged = sizeof(T) == 8 || MCT == 72 || MCT == 135 || MCT == 270;
+      const RowSource<C, Pair, ranged> src{spair, SH, H, M};
       // multiply by A_M between the transforms, in registers
       auto mul = [&](int j, int m, C z) -> C {
         T a0 = T(0), a1 = T(0);
