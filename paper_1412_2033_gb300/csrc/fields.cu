@@ -219,53 +219,70 @@ __device__ double shape_coeff(const Incl& in, int d, const int n[3]) {
 
 // tab1 (optional): the table of a second inclusion list with the same shapes
 // and centres (the coefficient 1/a beside a); each inclusion's shape factor and
-// phase are evaluated once for both.
+// phase are evaluated once for both.  Every shape factor is even in each
+// component of n (products of sinc for boxes, functions of |n| for disks and
+// spheres), so one thread takes n = (n_0, ...) with n_0 >= 0 together with
+// its mirror (-n_0, ...): each shape factor once, the phase of each entry as
+// before (the same operations per entry, so the same values).
 __global__ void coeff_kernel(double2* tab, double2* tab1, Geometry g, const Incl* incs, const Incl* incs1, int n,
                              double a0v, double a0v1) {
   const int d = g.d;
-  const int L0 = 2 * g.N[0] - 1;
+  const int N0 = g.N[0];
   const int L1 = (d == 3) ? 2 * g.N[1] - 1 : g.N[1];
   const int Ld = g.N[d - 1];   // half of 2N_d - 1: n_d = 0..N_d-1
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < g.table;
+  const int64_t rest = (d == 3) ? static_cast<int64_t>(L1) * Ld : Ld;   // entries per value of n_0
+  const int64_t half = static_cast<int64_t>(N0) * rest;                 // n_0 = 0 .. N_0-1
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < half;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    int nv[3] = {0, 0, 0};
+    const int64_t n0 = e / rest;
+    const int64_t rr = e - n0 * rest;
+    int nv[3] = {static_cast<int>(n0), 0, 0};
     if (d == 2) {
-      const int64_t i0 = e / Ld;
-      nv[0] = static_cast<int>(i0) - (g.N[0] - 1);
-      nv[1] = static_cast<int>(e - i0 * Ld);
+      nv[1] = static_cast<int>(rr);
     } else {
-      const int64_t pl = static_cast<int64_t>(L1) * Ld;
-      const int64_t i0 = e / pl;
-      const int64_t rem = e - i0 * pl;
-      const int64_t i1 = rem / Ld;
-      nv[0] = static_cast<int>(i0) - (g.N[0] - 1);
+      const int64_t i1 = rr / Ld;
       nv[1] = static_cast<int>(i1) - (g.N[1] - 1);
-      nv[2] = static_cast<int>(rem - i1 * Ld);
+      nv[2] = static_cast<int>(rr - i1 * Ld);
     }
-    (void)L0;
+    const int nm[3] = {-nv[0], nv[1], nv[2]};
+    const bool mirror = nv[0] != 0;
     const bool origin = nv[0] == 0 && nv[1] == 0 && nv[2] == 0;
     double re = origin ? a0v : 0.0, im = 0.0;
     double re1 = origin ? a0v1 : 0.0, im1 = 0.0;
+    double rem = 0.0, imm = 0.0, rem1 = 0.0, imm1 = 0.0;   // the mirror entry
     for (int i = 0; i < n; ++i) {
       const Incl in = incs[i];
+      const double sh = shape_coeff(in, d, nv);
+      const double f = in.dv * sh;
+      const double f1 = tab1 != nullptr ? incs1[i].dv * sh : 0.0;
       // exp(-2 pi i n.x_i): reduce n.x_i to [-1/2, 1/2] before the sincos
       double t = 0.0;
       for (int a = 0; a < d; ++a) t = fma(static_cast<double>(nv[a]), in.c[a], t);
       t -= rint(t);
       double s, c;
       sincospi(2.0 * t, &s, &c);
-      const double sh = shape_coeff(in, d, nv);
-      const double f = in.dv * sh;
       re += f * c;
       im -= f * s;
-      if (tab1 != nullptr) {
-        const double f1 = incs1[i].dv * sh;
-        re1 += f1 * c;
-        im1 -= f1 * s;
+      re1 += f1 * c;
+      im1 -= f1 * s;
+      if (mirror) {
+        double tm = 0.0;
+        for (int a = 0; a < d; ++a) tm = fma(static_cast<double>(nm[a]), in.c[a], tm);
+        tm -= rint(tm);
+        sincospi(2.0 * tm, &s, &c);
+        rem += f * c;
+        imm -= f * s;
+        rem1 += f1 * c;
+        imm1 -= f1 * s;
       }
     }
-    tab[e] = make_double2(re, im);
-    if (tab1 != nullptr) tab1[e] = make_double2(re1, im1);
+    const int64_t ep = (n0 + N0 - 1) * rest + rr, em = (N0 - 1 - n0) * rest + rr;
+    tab[ep] = make_double2(re, im);
+    if (tab1 != nullptr) tab1[ep] = make_double2(re1, im1);
+    if (mirror) {
+      tab[em] = make_double2(rem, imm);
+      if (tab1 != nullptr) tab1[em] = make_double2(rem1, imm1);
+    }
   }
 }
 
@@ -595,7 +612,8 @@ __global__ void add_constant_kernel(double2* v, const double2* e, FieldGeom fg, 
 // ---------------------------------------------------------------------------
 ghb_status launch_coeff_tables(double2* tab0, double2* tab1, const Geometry& g, const Incl* incs0,
                                const Incl* incs1, int n, double a0v0, double a0v1, cudaStream_t s) {
-  coeff_kernel<<<field_grid(g.table), kFieldThreads, 0, s>>>(tab0, tab1, g, incs0, incs1, n, a0v0, a0v1);
+  const int64_t half = static_cast<int64_t>(g.N[0]) * (g.table / (2 * g.N[0] - 1));   // n_0 >= 0
+  coeff_kernel<<<field_grid(half), kFieldThreads, 0, s>>>(tab0, tab1, g, incs0, incs1, n, a0v0, a0v1);
   GHB_CUDA_TRY(cudaGetLastError());
   return GHB_OK;
 }
